@@ -1,0 +1,551 @@
+/*
+ * Plain CPU oracle for h-clique clique-degrees, (k,Psi)-core decomposition
+ * and the CoreApp outputs (Fang et al., "Efficient Algorithms for Densest
+ * Subgraph Discovery", PVLDB 12(11), 2019).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header,
+ * table or helper with the CUDA library; it is deliberately slow and
+ * written to be checked against the paper by eye.
+ *
+ * Every function is single-threaded, uses plain C arrays and 64-bit
+ * unsigned counters, and returns 0 on success or a negative error code.
+ *
+ *   orc_build_csr            Sec. 2 "Data model": undirected, simple graph.
+ *   orc_clique_degrees       Def. 2 (clique instance), Def. 3 (clique-degree),
+ *                            Def. 4 (mu = number of instances).
+ *   orc_vertex_clique_degree Def. 3 for one vertex.
+ *   orc_core_decompose       Algorithm 3 ((k,Psi)-core decomposition), in the
+ *                            paper's steps: take a minimum clique-degree
+ *                            vertex v, record core[v] = deg[v], and for each
+ *                            clique instance containing v decrease every other
+ *                            member u whose clique-degree exceeds deg[v].
+ *   orc_threshold_prune      Def. 6 read directly: the (k,Psi)-core as what is
+ *                            left after repeatedly deleting every vertex with
+ *                            fewer than k clique instances (Sec. 4.3, opening
+ *                            paragraph).
+ *   orc_induced_clique_count mu(G[S]) for a vertex subset S (Def. 4).
+ *   orc_level_stats          For every distinct core value k: |R_k| and
+ *                            mu(R_k), with R_k = {v : core(v) >= k} (Def. 6,
+ *                            nestedness); one clique lies in R_k exactly when
+ *                            its smallest member core number is >= k.
+ *
+ * Clique instances are unordered vertex sets (Def. 2 and the remark after
+ * Def. 3).  Each set is listed exactly once as the increasing sequence
+ * v1 < v2 < ... < vh under one fixed total order of V; the oracle uses the
+ * order (degree, id), which only changes how long the listing takes.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+
+/* ---------------------------------------------------------------- CSR --- */
+
+static int cmp_u32(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Symmetric, sorted, duplicate-free CSR without self-loops.
+ * off: n+1 entries; adj: capacity 2*m.  Returns the number of adjacency
+ * entries written (2 * number of undirected edges) or a negative code. */
+int64_t orc_build_csr(uint32_t n, uint64_t m, const uint32_t* src,
+                      const uint32_t* dst, uint64_t* off, uint32_t* adj) {
+    uint64_t* cnt = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+    if (!cnt) return ORC_ENOMEM;
+    for (uint64_t i = 0; i < m; i++) {
+        if (src[i] >= n || dst[i] >= n) { free(cnt); return ORC_EINVAL; }
+        if (src[i] == dst[i]) continue;
+        cnt[src[i]]++;
+        cnt[dst[i]]++;
+    }
+    uint64_t* pos = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t* cur = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t tot = 0;
+    for (uint32_t v = 0; v < n; v++) tot += cnt[v];
+    uint32_t* tmp = (uint32_t*)malloc((size_t)(tot ? tot : 1) * sizeof(uint32_t));
+    if (!pos || !cur || !tmp) { free(cnt); free(pos); free(cur); free(tmp); return ORC_ENOMEM; }
+    pos[0] = 0;
+    for (uint32_t v = 0; v < n; v++) pos[v + 1] = pos[v] + cnt[v];
+    memcpy(cur, pos, ((size_t)n + 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < m; i++) {
+        uint32_t u = src[i], v = dst[i];
+        if (u == v) continue;
+        tmp[cur[u]++] = v;
+        tmp[cur[v]++] = u;
+    }
+    uint64_t k = 0;
+    off[0] = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        uint32_t* row = tmp + pos[v];
+        uint64_t len = pos[v + 1] - pos[v];
+        qsort(row, (size_t)len, sizeof(uint32_t), cmp_u32);
+        for (uint64_t j = 0; j < len; j++)
+            if (j == 0 || row[j] != row[j - 1]) adj[k++] = row[j];
+        off[v + 1] = k;
+    }
+    free(cnt); free(pos); free(cur); free(tmp);
+    return (int64_t)k;
+}
+
+/* ------------------------------------------- relabelled working graph --- */
+
+/* The working graph: vertices renamed so that new id order = (degree, id)
+ * order; rows sorted by new id.  old_of[new] and new_of[old] map back. */
+typedef struct {
+    uint32_t n;
+    uint64_t* off;
+    uint32_t* adj;
+    uint32_t* old_of;
+    uint32_t* new_of;
+    uint32_t maxdeg;
+} wgraph;
+
+static const uint64_t* g_sort_deg_off;
+static int cmp_by_deg_id(const void* a, const void* b) {
+    uint32_t x = *(const uint32_t*)a, y = *(const uint32_t*)b;
+    uint64_t dx = g_sort_deg_off[x + 1] - g_sort_deg_off[x];
+    uint64_t dy = g_sort_deg_off[y + 1] - g_sort_deg_off[y];
+    if (dx != dy) return (dx > dy) - (dx < dy);
+    return (x > y) - (x < y);
+}
+
+static void wg_free(wgraph* w) {
+    free(w->off); free(w->adj); free(w->old_of); free(w->new_of);
+    memset(w, 0, sizeof(*w));
+}
+
+static int wg_make(uint32_t n, const uint64_t* off, const uint32_t* adj, wgraph* w) {
+    memset(w, 0, sizeof(*w));
+    w->n = n;
+    uint64_t tot = off[n];
+    w->off = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    w->adj = (uint32_t*)malloc((size_t)(tot ? tot : 1) * sizeof(uint32_t));
+    w->old_of = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    w->new_of = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    if (!w->off || !w->adj || !w->old_of || !w->new_of) { wg_free(w); return ORC_ENOMEM; }
+    for (uint32_t v = 0; v < n; v++) w->old_of[v] = v;
+    g_sort_deg_off = off;
+    qsort(w->old_of, n, sizeof(uint32_t), cmp_by_deg_id);
+    for (uint32_t i = 0; i < n; i++) w->new_of[w->old_of[i]] = i;
+    w->off[0] = 0;
+    uint32_t md = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        uint32_t o = w->old_of[i];
+        uint64_t b = off[o], e = off[o + 1];
+        uint64_t base = w->off[i];
+        for (uint64_t j = b; j < e; j++) w->adj[base + (j - b)] = w->new_of[adj[j]];
+        qsort(w->adj + base, (size_t)(e - b), sizeof(uint32_t), cmp_u32);
+        w->off[i + 1] = base + (e - b);
+        if (e - b > md) md = (uint32_t)(e - b);
+    }
+    w->maxdeg = md;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------ sorted-set helpers --- */
+
+static int bsearch_u32(const uint32_t* a, uint64_t len, uint32_t x) {
+    uint64_t lo = 0, hi = len;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < len && a[lo] == x;
+}
+
+/* out = a intersect b (both sorted ascending); returns its size.  Iterates
+ * the shorter list and binary-searches the longer one. */
+static uint32_t intersect(const uint32_t* a, uint64_t na, const uint32_t* b,
+                          uint64_t nb, uint32_t* out) {
+    uint32_t k = 0;
+    if (na <= nb) {
+        for (uint64_t i = 0; i < na; i++) if (bsearch_u32(b, nb, a[i])) out[k++] = a[i];
+    } else {
+        for (uint64_t i = 0; i < nb; i++) if (bsearch_u32(a, na, b[i])) out[k++] = b[i];
+    }
+    return k;
+}
+
+/* Indexed binary min-heap over vertices keyed by (deg, tie), where tie is
+ * the vertex's original id (tie_order 0) or its complement (tie_order 1):
+ * the "sort"/"resort" steps of Algorithm 3 (the paper uses a bin-sort; any
+ * structure that yields a minimum clique-degree vertex computes the same
+ * core numbers). */
+typedef struct {
+    uint32_t* heap;
+    uint32_t* pos;
+    uint32_t size;
+    const uint64_t* key;
+    const uint32_t* tie;
+} vheap;
+
+static int vh_less(const vheap* H, uint32_t a, uint32_t b) {
+    if (H->key[a] != H->key[b]) return H->key[a] < H->key[b];
+    return H->tie[a] < H->tie[b];
+}
+static void vh_swap(vheap* H, uint32_t i, uint32_t j) {
+    uint32_t a = H->heap[i], b = H->heap[j];
+    H->heap[i] = b; H->heap[j] = a;
+    H->pos[b] = i; H->pos[a] = j;
+}
+static void vh_up(vheap* H, uint32_t i) {
+    while (i > 0) {
+        uint32_t p = (i - 1) / 2;
+        if (!vh_less(H, H->heap[i], H->heap[p])) break;
+        vh_swap(H, i, p);
+        i = p;
+    }
+}
+static void vh_down(vheap* H, uint32_t i) {
+    for (;;) {
+        uint32_t l = 2 * i + 1, r = l + 1, s = i;
+        if (l < H->size && vh_less(H, H->heap[l], H->heap[s])) s = l;
+        if (r < H->size && vh_less(H, H->heap[r], H->heap[s])) s = r;
+        if (s == i) break;
+        vh_swap(H, i, s);
+        i = s;
+    }
+}
+static uint32_t vh_pop(vheap* H) {
+    uint32_t top = H->heap[0];
+    H->size--;
+    if (H->size) {
+        H->heap[0] = H->heap[H->size];
+        H->pos[H->heap[0]] = 0;
+        vh_down(H, 0);
+    }
+    H->pos[top] = UINT32_MAX;
+    return top;
+}
+
+/* --------------------------------------------------- clique listing --- */
+
+/* A visitor receives every clique instance (as h new ids) once. */
+typedef struct lister lister;
+typedef void (*visit_fn)(lister* L, const uint32_t* clique);
+
+struct lister {
+    const wgraph* g;
+    int h;
+    uint32_t* tuple;     /* h entries */
+    uint32_t** cand;     /* h candidate buffers, each maxdeg+1 */
+    visit_fn visit;
+    /* visitor state */
+    uint64_t* deg;       /* per new id */
+    uint64_t mu;
+    vheap* heap;         /* peeling: bucket structure of Algorithm 3 */
+    const uint64_t* core;     /* level stats: core per new id */
+    const uint64_t* levels;   /* sorted distinct core values */
+    uint32_t nlevels;
+    uint64_t* level_hist;
+    uint64_t kthr;       /* threshold prune */
+    uint8_t* queued;
+    uint32_t* queue;
+    uint64_t qtail;
+};
+
+/* tuple[0..depth-1] is a clique; cand (sorted, ncand entries) holds every
+ * vertex after tuple[depth-1] adjacent to all of tuple[0..depth-1]. */
+static void extend(lister* L, int depth, const uint32_t* cand, uint32_t ncand) {
+    const wgraph* g = L->g;
+    for (uint32_t i = 0; i < ncand; i++) {
+        uint32_t x = cand[i];
+        L->tuple[depth] = x;
+        if (depth + 1 == L->h) {
+            L->visit(L, L->tuple);
+        } else {
+            uint32_t* nxt = L->cand[depth + 1];
+            uint32_t nn = intersect(cand + i + 1, ncand - i - 1,
+                                    g->adj + g->off[x], g->off[x + 1] - g->off[x], nxt);
+            if (nn + depth + 1 >= (uint32_t)L->h) extend(L, depth + 1, nxt, nn);
+        }
+    }
+}
+
+static int lister_init(lister* L, const wgraph* g, int h, visit_fn f) {
+    memset(L, 0, sizeof(*L));
+    L->g = g; L->h = h; L->visit = f;
+    L->tuple = (uint32_t*)calloc((size_t)h + 1, sizeof(uint32_t));
+    L->cand = (uint32_t**)calloc((size_t)h + 1, sizeof(uint32_t*));
+    if (!L->tuple || !L->cand) return ORC_ENOMEM;
+    for (int i = 0; i <= h; i++) {
+        L->cand[i] = (uint32_t*)malloc(((size_t)g->maxdeg + 1) * sizeof(uint32_t));
+        if (!L->cand[i]) return ORC_ENOMEM;
+    }
+    return ORC_OK;
+}
+
+static void lister_free(lister* L) {
+    if (L->cand) for (int i = 0; i <= L->h; i++) free(L->cand[i]);
+    free(L->cand); free(L->tuple);
+}
+
+/* Every h-clique of the whole graph, once (v1 < ... < vh in new ids). */
+static void list_all(lister* L) {
+    const wgraph* g = L->g;
+    for (uint32_t v = 0; v < g->n; v++) {
+        L->tuple[0] = v;
+        const uint32_t* row = g->adj + g->off[v];
+        uint64_t len = g->off[v + 1] - g->off[v];
+        uint64_t j = 0;
+        while (j < len && row[j] <= v) j++;        /* later neighbours only */
+        if (L->h == 1) { L->visit(L, L->tuple); continue; }
+        extend(L, 1, row + j, (uint32_t)(len - j));
+    }
+}
+
+/* Every h-clique that contains v, among vertices with alive[] != 0 (v is
+ * taken as alive): v plus an (h-1)-clique of the alive neighbours of v.
+ * The visitor sees the clique with v in slot 0. */
+static void list_containing(lister* L, uint32_t v, const uint8_t* alive) {
+    const wgraph* g = L->g;
+    uint32_t* c0 = L->cand[L->h];   /* spare buffer */
+    uint32_t k = 0;
+    for (uint64_t j = g->off[v]; j < g->off[v + 1]; j++) {
+        uint32_t u = g->adj[j];
+        if (!alive || alive[u]) c0[k++] = u;
+    }
+    L->tuple[0] = v;
+    if (L->h == 1) { L->visit(L, L->tuple); return; }
+    extend(L, 1, c0, k);
+}
+
+/* ----------------------------------------------------- Def. 3 / Def. 4 -- */
+
+static void visit_count(lister* L, const uint32_t* c) {
+    L->mu++;
+    for (int i = 0; i < L->h; i++) L->deg[c[i]]++;
+}
+
+static int check_h(int h) { return (h >= 2 && h <= 16) ? ORC_OK : ORC_EINVAL; }
+
+/* deg[v] = number of h-clique instances containing v (original ids);
+ * *mu = number of h-clique instances. */
+int orc_clique_degrees(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                       int h, uint64_t* deg, uint64_t* mu) {
+    if (check_h(h)) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    if (lister_init(&L, &g, h, visit_count)) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    L.deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    if (!L.deg) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    list_all(&L);
+    for (uint32_t i = 0; i < n; i++) deg[g.old_of[i]] = L.deg[i];
+    *mu = L.mu;
+    free(L.deg); lister_free(&L); wg_free(&g);
+    return ORC_OK;
+}
+
+/* deg(v, Psi) for one vertex v: the (h-1)-cliques among the neighbours. */
+int orc_vertex_clique_degree(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                             int h, uint32_t v, uint64_t* out) {
+    if (check_h(h) || v >= n) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    if (lister_init(&L, &g, h, visit_count)) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    L.deg = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));
+    if (!L.deg) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    list_containing(&L, g.new_of[v], NULL);
+    *out = L.mu;
+    free(L.deg); lister_free(&L); wg_free(&g);
+    return ORC_OK;
+}
+
+/* mu(G[S]) with S = {v : mask[v] != 0}. */
+int orc_induced_clique_count(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                             int h, const uint8_t* mask, uint64_t* mu) {
+    if (check_h(h)) return ORC_EINVAL;
+    /* Build G[S] as a CSR on the original ids (rows of vertices outside S
+     * are empty) and count its cliques. */
+    uint64_t* o2 = (uint64_t*)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t* a2 = (uint32_t*)malloc((size_t)(off[n] ? off[n] : 1) * sizeof(uint32_t));
+    uint64_t* d2 = (uint64_t*)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    if (!o2 || !a2 || !d2) { free(o2); free(a2); free(d2); return ORC_ENOMEM; }
+    uint64_t k = 0;
+    o2[0] = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        if (mask[v])
+            for (uint64_t j = off[v]; j < off[v + 1]; j++)
+                if (mask[adj[j]]) a2[k++] = adj[j];
+        o2[v + 1] = k;
+    }
+    int rc = orc_clique_degrees(n, o2, a2, h, d2, mu);
+    free(o2); free(a2); free(d2);
+    return rc;
+}
+
+/* ----------------------------------------------------- Algorithm 3 ----- */
+
+/* Lines 6-9 of Algorithm 3 for one clique instance containing the pivot v
+ * (slot 0): decrease each other member u whose clique-degree exceeds v's,
+ * and move u to its new place in the order at once (line 11). */
+static void visit_peel(lister* L, const uint32_t* c) {
+    uint64_t dv = L->deg[c[0]];
+    for (int i = 1; i < L->h; i++) {
+        uint32_t u = c[i];
+        if (L->deg[u] > dv) {
+            L->deg[u]--;
+            vh_up(L->heap, L->heap->pos[u]);
+        }
+    }
+}
+
+/* core[v] (original ids) and *kmax.  tie_order picks which of several
+ * minimum clique-degree vertices goes first (0: smallest id, 1: largest);
+ * the result must not depend on it. */
+int orc_core_decompose(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                       int h, int tie_order, uint64_t* core, uint64_t* kmax) {
+    if (check_h(h)) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    int rc = ORC_ENOMEM;
+    uint8_t* alive = NULL; uint32_t* tie = NULL; vheap H; memset(&H, 0, sizeof(H));
+    if (lister_init(&L, &g, h, visit_count)) goto out;
+    L.deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    alive = (uint8_t*)malloc((size_t)(n ? n : 1));
+    tie = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    H.heap = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    H.pos = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    if (!L.deg || !alive || !tie || !H.heap || !H.pos) goto out;
+    /* line 2: clique-degree of every vertex */
+    list_all(&L);
+    /* line 3: order by clique-degree */
+    for (uint32_t i = 0; i < n; i++) {
+        alive[i] = 1;
+        tie[i] = tie_order ? ~g.old_of[i] : g.old_of[i];
+    }
+    H.key = L.deg; H.tie = tie; H.size = n;
+    for (uint32_t i = 0; i < n; i++) { H.heap[i] = i; H.pos[i] = i; }
+    for (int64_t i = (int64_t)n / 2 - 1; i >= 0; i--) vh_down(&H, (uint32_t)i);
+    L.visit = visit_peel;
+    L.heap = &H;
+    uint64_t km = 0;
+    /* lines 4-11 */
+    while (H.size) {
+        uint32_t v = vh_pop(&H);
+        core[g.old_of[v]] = L.deg[v];                 /* line 5 */
+        if (L.deg[v] > km) km = L.deg[v];
+        list_containing(&L, v, alive);                /* lines 6-9, 11 */
+        alive[v] = 0;                                 /* line 10 */
+    }
+    *kmax = km;
+    rc = ORC_OK;
+out:
+    free(L.deg); free(alive); free(tie);
+    free(H.heap); free(H.pos);
+    lister_free(&L); wg_free(&g);
+    return rc;
+}
+
+/* -------------------------------------------- Def. 6 by pruning -------- */
+
+static void visit_prune(lister* L, const uint32_t* c) {
+    for (int i = 1; i < L->h; i++) {
+        uint32_t u = c[i];
+        L->deg[u]--;
+        if (L->deg[u] < L->kthr && !L->queued[u]) {
+            L->queued[u] = 1;
+            L->queue[L->qtail++] = u;
+        }
+    }
+}
+
+/* in_R[v] = 1 iff v is in the (k,Psi)-core R_k: delete vertices with fewer
+ * than k clique instances until none is left. */
+int orc_threshold_prune(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                        int h, uint64_t k, uint8_t* in_R) {
+    if (check_h(h)) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    int rc = ORC_ENOMEM;
+    uint8_t* alive = NULL;
+    if (lister_init(&L, &g, h, visit_count)) goto out;
+    L.deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    L.queued = (uint8_t*)calloc((size_t)(n ? n : 1), 1);
+    L.queue = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    alive = (uint8_t*)malloc((size_t)(n ? n : 1));
+    if (!L.deg || !L.queued || !L.queue || !alive) goto out;
+    list_all(&L);
+    L.kthr = k;
+    for (uint32_t v = 0; v < n; v++) {
+        alive[v] = 1;
+        if (L.deg[v] < k) { L.queued[v] = 1; L.queue[L.qtail++] = v; }
+    }
+    L.visit = visit_prune;
+    for (uint64_t qh = 0; qh < L.qtail; qh++) {
+        uint32_t v = L.queue[qh];
+        list_containing(&L, v, alive);
+        alive[v] = 0;
+    }
+    for (uint32_t i = 0; i < n; i++) in_R[g.old_of[i]] = alive[i];
+    rc = ORC_OK;
+out:
+    free(L.deg); free(L.queued); free(L.queue); free(alive);
+    lister_free(&L); wg_free(&g);
+    return rc;
+}
+
+/* ---------------------------------------------- level statistics ------- */
+
+static void visit_level(lister* L, const uint32_t* c) {
+    uint64_t lo = L->core[c[0]];
+    for (int i = 1; i < L->h; i++) if (L->core[c[i]] < lo) lo = L->core[c[i]];
+    /* index of lo among the sorted distinct levels */
+    uint32_t a = 0, b = L->nlevels;
+    while (a < b) {
+        uint32_t mid = a + (b - a) / 2;
+        if (L->levels[mid] < lo) a = mid + 1; else b = mid;
+    }
+    L->level_hist[a]++;
+}
+
+/* Given core[] (original ids) and the sorted distinct values levels[0..nl),
+ * write size[j] = |R_{levels[j]}| and mu[j] = mu(R_{levels[j]}). */
+int orc_level_stats(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
+                    const uint64_t* core, const uint64_t* levels, uint32_t nl,
+                    uint64_t* size, uint64_t* mu) {
+    if (check_h(h)) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    int rc = ORC_ENOMEM;
+    uint64_t* cw = NULL;
+    if (lister_init(&L, &g, h, visit_level)) goto out;
+    cw = (uint64_t*)malloc((size_t)(n ? n : 1) * sizeof(uint64_t));
+    L.level_hist = (uint64_t*)calloc((size_t)nl + 1, sizeof(uint64_t));
+    if (!cw || !L.level_hist) goto out;
+    for (uint32_t i = 0; i < n; i++) cw[i] = core[g.old_of[i]];
+    L.core = cw; L.levels = levels; L.nlevels = nl;
+    list_all(&L);
+    /* |R_k| counts vertices with core >= k: histogram by level, then
+     * suffix sums; mu(R_k) counts cliques whose smallest core is >= k. */
+    for (uint32_t j = 0; j < nl; j++) size[j] = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        uint32_t a = 0, b = nl;
+        while (a < b) {
+            uint32_t mid = a + (b - a) / 2;
+            if (levels[mid] < core[v]) a = mid + 1; else b = mid;
+        }
+        if (a < nl && levels[a] == core[v]) size[a]++;
+        else { rc = ORC_EINVAL; goto out; }
+    }
+    uint64_t acc = 0, accv = 0;
+    for (int64_t j = (int64_t)nl - 1; j >= 0; j--) {
+        acc += L.level_hist[j]; mu[j] = acc;
+        accv += size[j]; size[j] = accv;
+    }
+    rc = ORC_OK;
+out:
+    free(cw); free(L.level_hist);
+    lister_free(&L); wg_free(&g);
+    return rc;
+}
