@@ -1,0 +1,189 @@
+/*
+ * dsd.h -- C ABI of libdsd: h-clique clique-degrees, (k,Psi)-core
+ * decomposition and CoreApp outputs on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The operations follow Fang, Yu, Cheng, Lakshmanan, Lin, "Efficient
+ * Algorithms for Densest Subgraph Discovery", PVLDB 12(11), 2019:
+ *   - graph model: undirected, unweighted, simple (Sec. 2, "Data model");
+ *   - clique instance, clique-degree deg(v,Psi), mu(G,Psi), density
+ *     rho = mu/|V| (Sec. 2, Defs. 2-4; Problem 1);
+ *   - (k,Psi)-core R_k, clique-core number core(v,Psi), k_max
+ *     (Sec. 4.1, Def. 6);
+ *   - (k,Psi)-core decomposition (Sec. 4.3, Algorithm 3);
+ *   - IncApp / CoreApp output: the (k_max,Psi)-core (Sec. 5.2, Algorithms 5
+ *     and 6, Lemma 6), and the densest residual subgraph met while peeling
+ *     (Sec. 5.1, Pruning1), returned as the densest nested level set R_k.
+ *
+ * Conventions shared by every call:
+ *   - Vertex ids are uint32 in [0, n).  Per-vertex counters are uint64.
+ *   - h (the clique size |V_Psi|) must satisfy 2 <= h <= DSD_MAX_H.
+ *   - `mem` says where caller buffers live: DSD_MEM_HOST (pageable or pinned
+ *     host memory) or DSD_MEM_DEVICE (device memory of the graph's GPU).
+ *     Every output buffer is allocated and owned by the caller; the library
+ *     never frees caller memory and keeps no pointer to it after returning.
+ *   - Work is ordered on the graph's CUDA stream (given at creation, changed
+ *     with dsd_graph_set_stream).  A call with DSD_MEM_HOST outputs returns
+ *     after the results are in host memory; with DSD_MEM_DEVICE outputs it
+ *     may return before the stream has finished (synchronise the stream to
+ *     read them).
+ *   - Errors are returned as dsd_status, never thrown; dsd_last_error()
+ *     gives a message for the calling thread.  After DSD_ERR_CUDA or
+ *     DSD_ERR_TIMEOUT the graph handle should be destroyed.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Every call computes its result entirely on the GPU; there is no CPU
+ *     fallback.  Without a usable CUDA device calls return DSD_ERR_CUDA.
+ */
+#ifndef DSD_H
+#define DSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSD_MAX_H 8
+
+typedef enum {
+    DSD_OK = 0,
+    DSD_ERR_INVALID = 1,     /* bad argument: NULL pointer, h out of range, id >= n, ... */
+    DSD_ERR_NOMEM = 2,       /* device or host allocation failed */
+    DSD_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
+    DSD_ERR_TIMEOUT = 4,     /* a bounded inter-block wait ran out (see dsd_set_wait_limit_ms) */
+    DSD_ERR_OVERFLOW = 5,    /* a result does not fit the caller's buffer or a counter overflowed */
+    DSD_ERR_UNSUPPORTED = 6, /* input outside what this build handles (message says why) */
+    DSD_ERR_INTERNAL = 7
+} dsd_status;
+
+enum { DSD_MEM_HOST = 0, DSD_MEM_DEVICE = 1 };
+
+typedef struct dsd_graph dsd_graph;   /* opaque */
+
+/* ------------------------------------------------------------------ meta */
+
+const char* dsd_status_string(dsd_status s);
+/* Message for the last failed call on this thread ("" if none). */
+const char* dsd_last_error(void);
+/* Library version string. */
+const char* dsd_version(void);
+
+/* Upper bound, in milliseconds, on every inter-block wait inside a
+ * persistent kernel (grid barriers).  A wait that runs out makes the kernel
+ * record the fault, leave its loop, and the call return DSD_ERR_TIMEOUT.
+ * Default 20000 ms.  Applies to calls started afterwards, process-wide. */
+dsd_status dsd_set_wait_limit_ms(uint32_t ms);
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Build a graph from an edge list (Sec. 2 data model).  Edge i joins
+ * src[i] and dst[i]; the list may hold self-loops, repeated pairs and both
+ * orientations of a pair -- loops are dropped and each unordered pair is
+ * kept once.  src/dst: m entries each, in host or device memory per `mem`.
+ * `cuda_stream` is a cudaStream_t (NULL = the legacy default stream) on the
+ * current CUDA device; the graph lives on that device.
+ * Errors: DSD_ERR_INVALID if out == NULL, (m > 0 and src/dst NULL), or an
+ * endpoint >= n; DSD_ERR_NOMEM; DSD_ERR_CUDA. */
+dsd_status dsd_graph_from_edges(uint32_t n, uint64_t m, const uint32_t* src,
+                                const uint32_t* dst, int mem, void* cuda_stream,
+                                dsd_graph** out);
+
+/* Build a graph from a CSR: off[n+1] (off[0] = 0, non-decreasing), adj[off[n]].
+ * The CSR is cleaned exactly like an edge list (rows sorted, loops and
+ * repeats dropped) and symmetrised: an entry v in row u makes u,v adjacent.
+ * Errors: as dsd_graph_from_edges, plus DSD_ERR_INVALID for a malformed off[]. */
+dsd_status dsd_graph_from_csr(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                              int mem, void* cuda_stream, dsd_graph** out);
+
+/* Release a graph and all its device memory.  NULL is a no-op. */
+void dsd_graph_destroy(dsd_graph* g);
+
+/* n and the number m of undirected edges after cleaning.  Either pointer may
+ * be NULL. */
+dsd_status dsd_graph_info(const dsd_graph* g, uint32_t* n, uint64_t* m);
+
+/* Change the stream later calls on g are ordered on. */
+dsd_status dsd_graph_set_stream(dsd_graph* g, void* cuda_stream);
+
+/* Copy out the cleaned symmetric CSR: off[n+1], adj[2m] (rows ascending). */
+dsd_status dsd_graph_csr(dsd_graph* g, uint64_t* off, uint32_t* adj, int mem);
+
+/* ------------------------------------------------- ordering (h = 2 core) */
+
+/* Edge k-core numbers (Sec. 4.1, Def. 5) -- the (k,Psi)-core numbers for
+ * h = 2 -- and the degeneracy rank used to orient edges for listing:
+ * rank[v] in [0, n) orders vertices by (peeling round, id), where the
+ * peeling round is the level-synchronous round in which v left.  Either
+ * output may be NULL.  `degeneracy` (may be NULL) receives max core_2. */
+dsd_status dsd_degeneracy_order(dsd_graph* g, uint32_t* core2, uint32_t* rank,
+                                uint32_t* degeneracy, int mem);
+
+/* ------------------------------------------------------ clique-degrees */
+
+/* deg[v] = deg_G(v, Psi), the number of h-clique instances containing v
+ * (Def. 3), for all n vertices; *mu = mu(G, Psi) (Def. 4).  deg: n entries
+ * (may be NULL to get mu only); mu may be NULL.  Both live per `mem`.
+ * Errors: DSD_ERR_INVALID (h), DSD_ERR_UNSUPPORTED if h >= 4 and some
+ * vertex has more than 1024 higher-ranked neighbours (degeneracy > 1024). */
+dsd_status dsd_clique_degrees(dsd_graph* g, int h, uint64_t* deg, uint64_t* mu, int mem);
+
+/* ------------------------------------------------- core decomposition */
+
+/* core[v] = core_G(v, Psi) (Def. 6) for all n vertices, by level-synchronous
+ * peeling (Algorithm 3 with every minimum-degree vertex removed at once);
+ * *kmax = max core.  core (n entries) or kmax may be NULL.
+ * A graph with no h-clique has core = 0 everywhere and kmax = 0. */
+dsd_status dsd_core_decompose(dsd_graph* g, int h, uint64_t* core, uint64_t* kmax, int mem);
+
+/* Nested level statistics of the last decomposition run on g with this h
+ * (dsd_core_decompose or dsd_core_app): for each distinct core value k in
+ * increasing order, level_k[j] = k, level_size[j] = |R_k| and
+ * level_mu[j] = mu(R_k).  `cap` is the capacity of each array; *nlevels
+ * receives the number of levels (DSD_ERR_OVERFLOW if it exceeds cap; the
+ * first cap entries are still written).  Arrays may be NULL when cap = 0.
+ * DSD_ERR_INVALID if no decomposition with this h has run on g. */
+dsd_status dsd_level_stats(dsd_graph* g, int h, uint64_t* level_k, uint32_t* level_size,
+                           uint64_t* level_mu, uint32_t cap, uint32_t* nlevels, int mem);
+
+/* ------------------------------------------------------------- CoreApp */
+
+typedef struct {
+    uint64_t kmax;            /* maximum clique-core number k_max */
+    uint32_t kmax_core_size;  /* |R_kmax| */
+    uint32_t densest_size;    /* |S*| */
+    uint64_t kmax_core_mu;    /* mu(R_kmax) */
+    uint64_t best_k;          /* S* = R_best_k */
+    uint64_t densest_mu;      /* mu(S*); rho(S*) = densest_mu / densest_size exactly */
+    uint32_t nlevels;         /* number of distinct core values */
+    uint32_t reserved;
+} dsd_core_app_result;
+
+/* CoreApp / IncApp output (Algorithms 5 and 6, Lemma 6) plus Pruning1's
+ * densest residual (Sec. 5.1):
+ *   kmax_core: the vertices of the (k_max,Psi)-core, ascending;
+ *   densest:   S* = R_k maximising rho(R_k) = mu(R_k)/|R_k| over the
+ *              distinct levels k (ties: the largest k), ascending.
+ * Each vertex array needs capacity n (may be NULL to skip it); r must not
+ * be NULL.  With no h-clique: kmax = 0 and both sets are all of V, density
+ * 0/n (the whole graph is the (0,Psi)-core, Example 3).  With n = 0 all
+ * sizes are 0. */
+dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
+                        int mem, dsd_core_app_result* r);
+
+/* ---------------------------------------------------------- profiling */
+
+/* Per-phase device timings (CUDA events on the graph's stream) of the most
+ * recent calls on g.  Enable with dsd_set_profiling(g, 1).  Phases:
+ *   0 csr build, 1 degeneracy peel (h = 2), 2 orientation, 3 clique count,
+ *   4 (k,Psi) peel, 5 output extraction.
+ * ms[p] is the time of the last run of phase p; bytes[p] the algorithmic
+ * bytes that run moved (model in the project documentation; 0 if none);
+ * launches[p] the number of kernels it launched. */
+#define DSD_NPHASES 6
+dsd_status dsd_set_profiling(dsd_graph* g, int on);
+dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSD_H */

@@ -1,0 +1,328 @@
+"""ctypes binding of libdsd (include/dsd.h).
+
+Argument marshalling only: every computation runs in the CUDA library.
+The module-level ``dsd_*`` functions mirror the C entry points one to one
+(pointers are passed as integers); :class:`Graph` is a thin convenience
+wrapper that allocates outputs as numpy arrays (host) or torch CUDA tensors
+(device).  If the compiled library is missing, importing the wrappers raises
+an error -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdsd.so")
+
+DSD_MEM_HOST = 0
+DSD_MEM_DEVICE = 1
+DSD_NPHASES = 6
+PHASES = ("csr", "order_peel", "orient", "count", "peel", "extract")
+
+STATUS = {0: "DSD_OK", 1: "DSD_ERR_INVALID", 2: "DSD_ERR_NOMEM", 3: "DSD_ERR_CUDA",
+          4: "DSD_ERR_TIMEOUT", 5: "DSD_ERR_OVERFLOW", 6: "DSD_ERR_UNSUPPORTED",
+          7: "DSD_ERR_INTERNAL"}
+
+
+class DSDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class CoreAppResult(ctypes.Structure):
+    _fields_ = [("kmax", ctypes.c_uint64), ("kmax_core_size", ctypes.c_uint32),
+                ("densest_size", ctypes.c_uint32), ("kmax_core_mu", ctypes.c_uint64),
+                ("best_k", ctypes.c_uint64), ("densest_mu", ctypes.c_uint64),
+                ("nlevels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_int = ctypes.c_int
+
+SIGNATURES = {
+    "dsd_status_string": (ctypes.c_char_p, [_int]),
+    "dsd_last_error": (ctypes.c_char_p, []),
+    "dsd_version": (ctypes.c_char_p, []),
+    "dsd_set_wait_limit_ms": (_int, [_u32]),
+    "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
+    "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
+    "dsd_graph_destroy": (None, [_P]),
+    "dsd_graph_info": (_int, [_P, _P, _P]),
+    "dsd_graph_set_stream": (_int, [_P, _P]),
+    "dsd_graph_csr": (_int, [_P, _P, _P, _int]),
+    "dsd_degeneracy_order": (_int, [_P, _P, _P, _P, _int]),
+    "dsd_clique_degrees": (_int, [_P, _int, _P, _P, _int]),
+    "dsd_core_decompose": (_int, [_P, _int, _P, _P, _int]),
+    "dsd_level_stats": (_int, [_P, _int, _P, _P, _P, _u32, _P, _int]),
+    "dsd_core_app": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult)]),
+    "dsd_set_profiling": (_int, [_P, _int]),
+    "dsd_phase_stats": (_int, [_P, _P, _P, _P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libdsd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdsd.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = load()
+        raise DSDError(rc, (lib.dsd_last_error() or b"").decode())
+
+
+# ----------------------------------------------------- raw C entry points
+
+def dsd_status_string(s):
+    return load().dsd_status_string(s).decode()
+
+
+def dsd_last_error():
+    return load().dsd_last_error().decode()
+
+
+def dsd_version():
+    return load().dsd_version().decode()
+
+
+def dsd_set_wait_limit_ms(ms):
+    _check(load().dsd_set_wait_limit_ms(ms))
+
+
+def dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr):
+    out = _P()
+    _check(load().dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr, ctypes.byref(out)))
+    return out.value
+
+
+def dsd_graph_from_csr(n, off_ptr, adj_ptr, mem, stream_ptr):
+    out = _P()
+    _check(load().dsd_graph_from_csr(n, off_ptr, adj_ptr, mem, stream_ptr, ctypes.byref(out)))
+    return out.value
+
+
+def dsd_graph_destroy(g):
+    load().dsd_graph_destroy(g)
+
+
+def dsd_graph_info(g):
+    n = _u32()
+    m = _u64()
+    _check(load().dsd_graph_info(g, ctypes.addressof(n), ctypes.addressof(m)))
+    return n.value, m.value
+
+
+def dsd_graph_set_stream(g, stream_ptr):
+    _check(load().dsd_graph_set_stream(g, stream_ptr))
+
+
+def dsd_graph_csr(g, off_ptr, adj_ptr, mem):
+    _check(load().dsd_graph_csr(g, off_ptr, adj_ptr, mem))
+
+
+def dsd_degeneracy_order(g, core2_ptr, rank_ptr, degen_ptr, mem):
+    _check(load().dsd_degeneracy_order(g, core2_ptr, rank_ptr, degen_ptr, mem))
+
+
+def dsd_clique_degrees(g, h, deg_ptr, mu_ptr, mem):
+    _check(load().dsd_clique_degrees(g, h, deg_ptr, mu_ptr, mem))
+
+
+def dsd_core_decompose(g, h, core_ptr, kmax_ptr, mem):
+    _check(load().dsd_core_decompose(g, h, core_ptr, kmax_ptr, mem))
+
+
+def dsd_level_stats(g, h, k_ptr, size_ptr, mu_ptr, cap, nlevels_ptr, mem):
+    _check(load().dsd_level_stats(g, h, k_ptr, size_ptr, mu_ptr, cap, nlevels_ptr, mem))
+
+
+def dsd_core_app(g, h, kcore_ptr, densest_ptr, mem):
+    r = CoreAppResult()
+    _check(load().dsd_core_app(g, h, kcore_ptr, densest_ptr, mem, ctypes.byref(r)))
+    return r
+
+
+def dsd_set_profiling(g, on):
+    _check(load().dsd_set_profiling(g, 1 if on else 0))
+
+
+def dsd_phase_stats(g):
+    ms = (ctypes.c_float * DSD_NPHASES)()
+    by = (ctypes.c_uint64 * DSD_NPHASES)()
+    la = (ctypes.c_uint32 * DSD_NPHASES)()
+    _check(load().dsd_phase_stats(g, ctypes.addressof(ms), ctypes.addressof(by),
+                                  ctypes.addressof(la)))
+    return list(ms), list(by), list(la)
+
+
+# -------------------------------------------------------- convenience
+
+def _np_ptr(a):
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    """Owns one dsd_graph handle.  ``mem`` selects host (numpy) or device
+    (torch CUDA tensors) outputs for the query methods."""
+
+    def __init__(self, handle, stream_ptr, keepalive=()):
+        self.handle = handle
+        self.stream_ptr = stream_ptr
+        self._keep = keepalive
+        self.n, self.m = dsd_graph_info(handle)
+
+    # construction -----------------------------------------------------
+    @classmethod
+    def from_edges(cls, n, src, dst, stream=None):
+        sp = _stream_ptr(stream)
+        if hasattr(src, "is_cuda") and src.is_cuda:
+            src = src.contiguous()
+            dst = dst.contiguous()
+            h = dsd_graph_from_edges(n, src.numel(), src.data_ptr(), dst.data_ptr(),
+                                     DSD_MEM_DEVICE, sp)
+        else:
+            src = np.ascontiguousarray(src, np.uint32)
+            dst = np.ascontiguousarray(dst, np.uint32)
+            h = dsd_graph_from_edges(n, src.size, _np_ptr(src), _np_ptr(dst), DSD_MEM_HOST, sp)
+        return cls(h, sp)
+
+    @classmethod
+    def from_csr(cls, n, off, adj, stream=None):
+        sp = _stream_ptr(stream)
+        if hasattr(off, "is_cuda") and off.is_cuda:
+            h = dsd_graph_from_csr(n, off.data_ptr(), adj.data_ptr(), DSD_MEM_DEVICE, sp)
+        else:
+            off = np.ascontiguousarray(off, np.uint64)
+            adj = np.ascontiguousarray(adj, np.uint32)
+            h = dsd_graph_from_csr(n, _np_ptr(off), _np_ptr(adj) if adj.size else 0,
+                                   DSD_MEM_HOST, sp)
+        return cls(h, sp)
+
+    def close(self):
+        if self.handle:
+            dsd_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # buffers ------------------------------------------------------------
+    @staticmethod
+    def _alloc(count, kind, mem):
+        if mem == "host":
+            return np.zeros(max(count, 1), np.uint64 if kind == 8 else np.uint32)
+        import torch
+        return torch.zeros(max(count, 1), dtype=torch.int64 if kind == 8 else torch.int32,
+                           device="cuda")
+
+    @staticmethod
+    def _ptr(buf):
+        return _np_ptr(buf) if isinstance(buf, np.ndarray) else buf.data_ptr()
+
+    @staticmethod
+    def _memc(mem):
+        return DSD_MEM_HOST if mem == "host" else DSD_MEM_DEVICE
+
+    # queries --------------------------------------------------------------
+    def csr(self, mem="host"):
+        off = self._alloc(self.n + 1, 8, mem)
+        adj = self._alloc(2 * self.m, 4, mem)
+        dsd_graph_csr(self.handle, self._ptr(off), self._ptr(adj), self._memc(mem))
+        return off[: self.n + 1], adj[: 2 * self.m]
+
+    def degeneracy_order(self, mem="host"):
+        core2 = self._alloc(self.n, 4, mem)
+        rank = self._alloc(self.n, 4, mem)
+        dg = np.zeros(1, np.uint32)
+        dsd_degeneracy_order(self.handle, self._ptr(core2), self._ptr(rank), _np_ptr(dg),
+                             DSD_MEM_HOST if mem == "host" else DSD_MEM_DEVICE) \
+            if mem == "host" else \
+            dsd_degeneracy_order(self.handle, self._ptr(core2), self._ptr(rank), 0, DSD_MEM_DEVICE)
+        return core2[: self.n], rank[: self.n], int(dg[0])
+
+    def clique_degrees(self, h, mem="host"):
+        deg = self._alloc(self.n, 8, mem)
+        mu = self._alloc(1, 8, mem)
+        dsd_clique_degrees(self.handle, h, self._ptr(deg), self._ptr(mu), self._memc(mem))
+        return deg[: self.n], int(mu[0])
+
+    def core_decompose(self, h, mem="host"):
+        core = self._alloc(self.n, 8, mem)
+        km = np.zeros(1, np.uint64)
+        dsd_core_decompose(self.handle, h, self._ptr(core), _np_ptr(km), DSD_MEM_HOST) \
+            if mem == "host" else None
+        if mem != "host":
+            kmd = self._alloc(1, 8, mem)
+            dsd_core_decompose(self.handle, h, self._ptr(core), self._ptr(kmd), DSD_MEM_DEVICE)
+            km[0] = int(kmd[0])
+        return core[: self.n], int(km[0])
+
+    def level_stats(self, h):
+        nl = np.zeros(1, np.uint32)
+        cap = self.n + 1
+        k = np.zeros(cap, np.uint64)
+        s = np.zeros(cap, np.uint32)
+        mu = np.zeros(cap, np.uint64)
+        dsd_level_stats(self.handle, h, _np_ptr(k), _np_ptr(s), _np_ptr(mu), cap, _np_ptr(nl),
+                        DSD_MEM_HOST)
+        c = int(nl[0])
+        return k[:c], s[:c], mu[:c]
+
+    def core_app(self, h, mem="host", sets=True):
+        kc = self._alloc(self.n, 4, mem) if sets else None
+        de = self._alloc(self.n, 4, mem) if sets else None
+        r = dsd_core_app(self.handle, h, self._ptr(kc) if sets else 0,
+                         self._ptr(de) if sets else 0, self._memc(mem))
+        out = dict(kmax=int(r.kmax), kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                   densest_mu=int(r.densest_mu), densest_size=int(r.densest_size),
+                   kmax_core_size=int(r.kmax_core_size), nlevels=int(r.nlevels))
+        if sets:
+            out["kmax_core"] = kc[: r.kmax_core_size]
+            out["densest"] = de[: r.densest_size]
+        return out
+
+    def set_profiling(self, on=True):
+        dsd_set_profiling(self.handle, on)
+
+    def phase_stats(self):
+        ms, by, la = dsd_phase_stats(self.handle)
+        return {p: dict(ms=ms[i], bytes=by[i], launches=la[i]) for i, p in enumerate(PHASES)}

@@ -1,0 +1,300 @@
+// K4: h-clique clique-degrees (Def. 3) and mu (Def. 4) over the
+// degeneracy-oriented graph.
+//
+// Every h-clique is listed once, from its lowest-ranked vertex u: it is u
+// plus an (h-1)-clique inside N+(u) (vertices are relabelled so that rank =
+// id, hence N+(u) is the tail of u's sorted row).  Per vertex u the kernel
+// solves the sub-problem of cliques.cuh with root {u}, C = N+(u),
+// r = h - 1, and credits the counts with one atomic per (u, x) pair.
+//
+// Tiers by |N+(u)|:
+//   S  <= 32   : one warp per vertex, one-word bitmap rows, lane-level DFS;
+//   M  <= 1024 : one block per vertex, 32-word bitmap rows in shared memory;
+//   L  >  1024 : h = 3 only (no bitmap needed), one block per vertex.
+// For h = 3 (r = 2) the rows are never materialised: each hit of the row
+// scan is a triangle and is counted on the spot.
+#include "cliques.cuh"
+#include "graph.cuh"
+
+namespace dsd {
+namespace {
+
+constexpr int kCountThreads = 256;
+
+struct CountArgs {
+    uint32_t n;
+    int r;  // h - 1
+    const uint64_t* off;
+    const uint32_t* adj;
+    const uint64_t* split;
+    unsigned long long* deg;
+    unsigned long long* mu;
+    uint32_t* listM;      // vertices of tier M
+    uint32_t* listL;      // vertices of tier L
+    uint32_t* cntML;      // [2]
+    uint32_t* work;       // [1] dynamic queue for tier S
+};
+
+// Tier S + classification.  One warp per vertex.
+__global__ void __launch_bounds__(kCountThreads) k_count_small(CountArgs A) {
+    __shared__ uint32_t sC[kCountThreads / 32][32];
+    __shared__ uint32_t sRows[kCountThreads / 32][32];
+    __shared__ unsigned sCnt[kCountThreads / 32][32];
+    unsigned lane = lane_id(), w = warp_id();
+    uint32_t* C = sC[w];
+    uint32_t* rows = sRows[w];
+    unsigned* cnt = sCnt[w];
+    unsigned long long mu_acc = 0;
+    const uint32_t chunk = 32;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(A.work, chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= A.n) break;
+        uint32_t end = base + chunk < A.n ? base + chunk : A.n;
+        for (uint32_t u = base; u < end; u++) {
+            uint64_t b = A.split[u], e = A.off[u + 1];
+            uint32_t d = (uint32_t)(e - b);
+            if (d < (uint32_t)A.r) continue;            // cannot host a clique
+            if (d > 32) {
+                if (lane == 0) {
+                    if (d <= kBitmapMax || A.r == 2) {
+                        int which = d <= kBitmapMax ? 0 : 1;
+                        uint32_t at = atomicAdd(&A.cntML[which], 1u);
+                        (which ? A.listL : A.listM)[at] = u;
+                    } else {
+                        atomicAdd(&A.cntML[2], 1u);     // unsupported
+                    }
+                }
+                continue;
+            }
+            if (lane < d) { C[lane] = A.adj[b + lane]; cnt[lane] = 0; }
+            __syncwarp();
+            unsigned long long tot;
+            if (A.r == 2) {
+                // triangles: hits of row i are the third members
+                unsigned long long t = 0;
+                for (uint32_t i = 0; i < d; i++) {
+                    uint32_t x = C[i];
+                    uint64_t xb = A.split[x], xe = A.off[x + 1];
+                    unsigned hits = 0;
+                    for (uint64_t p = xb + lane; p < xe; p += 32) {
+                        uint32_t y = A.adj[p];
+                        uint32_t pos = (uint32_t)lower_bound_u32(C, d, y);
+                        if (pos < d && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
+                    }
+                    hits = __reduce_add_sync(0xffffffffu, hits);
+                    if (lane == 0 && hits) { atomicAdd(&cnt[i], hits); }
+                    t += hits;
+                }
+                tot = t;
+            } else {
+                warp_build_rows32(C, d, A.off, A.adj, A.split, rows);
+                tot = warp_dfs32(rows, d, A.r, cnt);
+            }
+            __syncwarp();
+            if (tot) {
+                if (lane < d && cnt[lane]) atomicAdd(&A.deg[C[lane]], (unsigned long long)cnt[lane]);
+                if (lane == 0) {
+                    atomicAdd(&A.deg[u], tot);
+                    mu_acc += tot;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && mu_acc) atomicAdd(A.mu, mu_acc);
+}
+
+// Tier M: one block per vertex, |N+(u)| in (32, 1024].
+__global__ void __launch_bounds__(kCountThreads) k_count_medium(CountArgs A) {
+    extern __shared__ uint32_t smem[];
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // 1024
+    uint32_t* C = smem + 2 * kBitmapMax;      // 1024
+    uint32_t* rows = smem + 3 * kBitmapMax;   // up to 1024*32 (only if r >= 3)
+    __shared__ unsigned long long s_tot;
+    uint32_t nM = A.cntML[0];
+    for (uint32_t it = blockIdx.x; it < nM; it += gridDim.x) {
+        uint32_t u = A.listM[it];
+        uint64_t b = A.split[u], e = A.off[u + 1];
+        uint32_t d = (uint32_t)(e - b);
+        uint32_t W = (d + 31) >> 5;
+        for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) { C[i] = A.adj[b + i]; cnt[i] = 0; }
+        if (A.r >= 3)
+            for (uint32_t i = threadIdx.x; i < d * W; i += blockDim.x) rows[i] = 0;
+        if (threadIdx.x == 0) s_tot = 0;
+        __syncthreads();
+        unsigned long long mine = 0;
+        if (A.r == 2) {
+            unsigned lane = lane_id(), nw = blockDim.x >> 5;
+            for (uint32_t i = warp_id(); i < d; i += nw) {
+                uint32_t x = C[i];
+                uint64_t xb = A.split[x], xe = A.off[x + 1];
+                unsigned hits = 0;
+                for (uint64_t p = xb + lane; p < xe; p += 32) {
+                    uint32_t y = A.adj[p];
+                    uint32_t pos = (uint32_t)lower_bound_u32(C, d, y);
+                    if (pos < d && C[pos] == y) { atomicAdd(&cnt[pos], 1ull); hits++; }
+                }
+                hits = __reduce_add_sync(0xffffffffu, hits);
+                if (lane == 0 && hits) atomicAdd(&cnt[i], (unsigned long long)hits);
+                if (lane == 0) mine += hits;
+            }
+        } else {
+            block_build_rows(C, d, W, A.off, A.adj, A.split, rows);
+            __syncthreads();
+            mine = block_dfs(rows, d, W, A.r, cnt);
+        }
+        if (mine) atomicAdd(&s_tot, mine);
+        __syncthreads();
+        unsigned long long tot = s_tot;
+        if (tot) {
+            for (uint32_t i = threadIdx.x; i < d; i += blockDim.x)
+                if (cnt[i]) atomicAdd(&A.deg[C[i]], cnt[i]);
+            if (threadIdx.x == 0) {
+                atomicAdd(&A.deg[u], tot);
+                atomicAdd(A.mu, tot);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Tier L (h = 3 only): |N+(u)| > 1024; candidates stay in global memory and
+// the credits go straight to the global counters.
+__global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
+    __shared__ unsigned long long s_tot;
+    uint32_t nL = A.cntML[1];
+    unsigned lane = lane_id(), nw = blockDim.x >> 5;
+    for (uint32_t it = blockIdx.x; it < nL; it += gridDim.x) {
+        uint32_t u = A.listL[it];
+        uint64_t b = A.split[u], e = A.off[u + 1];
+        uint32_t d = (uint32_t)(e - b);
+        const uint32_t* C = A.adj + b;
+        if (threadIdx.x == 0) s_tot = 0;
+        __syncthreads();
+        unsigned long long mine = 0;
+        for (uint32_t i = warp_id(); i < d; i += nw) {
+            uint32_t x = C[i];
+            uint64_t xb = A.split[x], xe = A.off[x + 1];
+            unsigned hits = 0;
+            for (uint64_t p = xb + lane; p < xe; p += 32) {
+                uint32_t y = A.adj[p];
+                uint64_t pos = lower_bound_u32(C, d, y);
+                if (pos < d && C[pos] == y) { atomicAdd(&A.deg[y], 1ull); hits++; }
+            }
+            hits = __reduce_add_sync(0xffffffffu, hits);
+            if (lane == 0 && hits) { atomicAdd(&A.deg[x], (unsigned long long)hits); mine += hits; }
+        }
+        if (mine) atomicAdd(&s_tot, mine);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_tot) {
+            atomicAdd(&A.deg[u], s_tot);
+            atomicAdd(A.mu, s_tot);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_degree_as_count(uint32_t n, const uint64_t* off, unsigned long long* deg) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        deg[v] = off[v + 1] - off[v];
+}
+
+// Algorithmic bytes of the h = 3 listing (documented model): offsets and
+// split read once per vertex, each N+(u) read once, each N+(x) read once per
+// oriented edge (u, x), one 8-byte read-modify-write per credited counter.
+__global__ void k_count_bytes3(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                               const uint64_t* split, unsigned long long* out) {
+    unsigned long long acc = 0;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        uint64_t b = split[u], e = off[u + 1];
+        acc += 16 + 4 * (e - b);              // off + split, N+(u)
+        for (uint64_t p = b; p < e; p++) {
+            uint32_t x = adj[p];
+            acc += 16 + 4 * (off[x + 1] - split[x]);   // off/split of x, N+(x)
+            acc += 16;                                  // counter of x
+        }
+        acc += 16;                                      // counter of u
+    }
+    acc = warp_sum(acc);
+    if (lane_id() == 0) atomicAdd(out, acc);
+}
+
+}  // namespace
+
+dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
+                         unsigned long long* mu_dev) {
+    cudaStream_t s = g->stream;
+    int sms = 152;
+    DSD_TRY(num_sms(&sms));
+    uint32_t n = g->n;
+    DSD_CU(cudaMemsetAsync(deg_new, 0, (size_t)n * 8 + 8, s));
+    DSD_CU(cudaMemsetAsync(mu_dev, 0, 8, s));
+    if (n == 0) return DSD_OK;
+    if (h == 2) {
+        k_degree_as_count<<<sms * 8, 256, 0, s>>>(n, g->roff, deg_new);
+        DSD_LAUNCHED();
+        unsigned long long m2 = g->m;
+        DSD_CU(cudaMemcpyAsync(mu_dev, &m2, 8, cudaMemcpyHostToDevice, s));
+        DSD_CU(cudaStreamSynchronize(s));
+        return DSD_OK;
+    }
+    CountArgs A;
+    A.n = n;
+    A.r = h - 1;
+    A.off = g->roff;
+    A.adj = g->radj;
+    A.split = g->rsplit;
+    A.deg = deg_new;
+    A.mu = mu_dev;
+    uint32_t* ws = nullptr;
+    DSD_TRY(dalloc(&ws, (size_t)2 * n + 8, s));
+    A.listM = ws;
+    A.listL = ws + n;
+    A.cntML = ws + 2 * (size_t)n;
+    A.work = A.cntML + 4;
+    dsd_status st = DSD_OK;
+    cudaError_t e = cudaMemsetAsync(A.cntML, 0, 8 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) {
+        k_count_small<<<sms * 8, kCountThreads, 0, s>>>(A);
+        size_t smemM = (size_t)3 * kBitmapMax * 4 + (h >= 4 ? (size_t)kBitmapMax * 32 * 4 : 0);
+        if (smemM > 48 * 1024)
+            cudaFuncSetAttribute(k_count_medium, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smemM);
+        k_count_medium<<<sms * (h >= 4 ? 1 : 4), kCountThreads, smemM, s>>>(A);
+        if (h == 3) k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A);
+        e = cudaGetLastError();
+    }
+    uint32_t unsupported = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&unsupported, A.cntML + 2, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(ws, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clique count", __FILE__, __LINE__);
+    if (unsupported) {
+        set_error("h=%d listing needs at most %u higher-ranked neighbours per vertex; %u vertices "
+                  "exceed it (degeneracy %u)", h, kBitmapMax, unsupported, g->degeneracy);
+        return DSD_ERR_UNSUPPORTED;
+    }
+    g->prof_launches[kPhaseCount] = h == 3 ? 3 : 2;
+    return st;
+}
+
+dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out) {
+    cudaStream_t s = g->stream;
+    unsigned long long* d = nullptr;
+    DSD_TRY(dalloc(&d, 1, s));
+    DSD_CU(cudaMemsetAsync(d, 0, 8, s));
+    int sms = 152;
+    num_sms(&sms);
+    k_count_bytes3<<<sms * 8, 256, 0, s>>>(g->n, g->roff, g->radj, g->rsplit, d);
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "count bytes", __FILE__, __LINE__);
+    *out = h + 8ull * g->n;   // + mu/counters initialisation is not counted; deg zero-fill
+    return DSD_OK;
+}
+
+}  // namespace dsd

@@ -1,0 +1,94 @@
+// The graph handle and the internal entry points of each stage.
+#pragma once
+
+#include "common.cuh"
+
+enum {
+    kPhaseCsr = 0,
+    kPhaseOrderPeel = 1,
+    kPhaseOrient = 2,
+    kPhaseCount = 3,
+    kPhasePeel = 4,
+    kPhaseExtract = 5,
+};
+
+struct dsd_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t n = 0;
+    uint64_t m = 0;               // undirected edges after cleaning
+
+    // cleaned CSR in the caller's vertex ids (rows ascending)
+    uint64_t* off = nullptr;      // [n+1]
+    uint32_t* adj = nullptr;      // [2m]
+
+    // degeneracy ordering (h = 2 peel) and the relabelled CSR
+    bool ordered = false;
+    uint64_t* core2 = nullptr;    // [n] edge core numbers, caller ids
+    uint32_t* rnd = nullptr;      // [n] peeling round, caller ids
+    uint32_t* new_of = nullptr;   // [n] caller id -> rank
+    uint32_t* old_of = nullptr;   // [n] rank -> caller id
+    uint64_t* roff = nullptr;     // [n+1] relabelled CSR (ids = ranks)
+    uint32_t* radj = nullptr;     // [2m]
+    uint64_t* rsplit = nullptr;   // [n] first entry of N+(v) in radj
+    uint32_t degeneracy = 0;
+    uint32_t maxdplus = 0;        // max |N+(v)|
+    uint64_t order_kmax = 0;
+
+    // levels of the h = 2 peel (caller ids space; levels are id-free)
+    uint32_t nlevels2 = 0;
+    uint64_t* lvl2_k = nullptr;
+    uint32_t* lvl2_size = nullptr;
+    uint64_t* lvl2_mu = nullptr;
+
+    // results of the last (k,Psi) decomposition with h >= 3
+    int last_h = 0;
+    uint64_t* core = nullptr;     // [n] caller ids
+    uint64_t last_kmax = 0;
+    uint64_t last_mu = 0;
+    uint32_t nlevels = 0;
+    uint64_t* lvl_k = nullptr;    // [n+1]
+    uint32_t* lvl_size = nullptr;
+    uint64_t* lvl_mu = nullptr;
+
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[2 * 6] = {};
+    float prof_ms[6] = {};
+    uint64_t prof_bytes[6] = {};
+    uint32_t prof_launches[6] = {};
+};
+
+namespace dsd {
+
+// CSR construction (K1).  src/dst on the device.
+dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32_t* dst);
+
+// Degeneracy order + relabelled CSR (K2 + K3), cached on g.
+dsd_status ensure_order(dsd_graph* g);
+
+// K4 on the relabelled graph: deg_new[rank] and *mu_dev (device pointers).
+dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
+                         unsigned long long* mu_dev);
+dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out);
+
+// Level-synchronous (k,Psi)-core peeling (K5/K6).
+struct PeelResult {
+    uint64_t kmax = 0;
+    uint32_t nlevels = 0;
+    uint32_t rounds = 0;
+    uint64_t items = 0;       // frontier work items processed
+};
+// off/adj/split: CSR in the working id space (split may be null for h = 2).
+// deg: [n] clique-degrees in, destroyed on return.  core/rnd: [n] outputs
+// (rnd may be null).  lvl_*: [n+1] level records.
+dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const uint32_t* adj,
+                    const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
+                    uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
+                    uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res);
+
+// Profiling helpers.
+void prof_begin(dsd_graph* g, int phase);
+void prof_end(dsd_graph* g, int phase);
+
+}  // namespace dsd
