@@ -67,6 +67,10 @@ const char* dsd_status_string(dsd_status s);
 const char* dsd_last_error(void);
 /* Library version string. */
 const char* dsd_version(void);
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all devices, all handles); the difference across a region counts the
+ * launches inside it. */
+uint64_t dsd_kernel_launches(void);
 
 /* Upper bound, in milliseconds, on every inter-block wait inside a
  * persistent kernel (grid barriers).  A wait that runs out makes the kernel

@@ -52,6 +52,7 @@ SIGNATURES = {
     "dsd_status_string": (ctypes.c_char_p, [_int]),
     "dsd_last_error": (ctypes.c_char_p, []),
     "dsd_version": (ctypes.c_char_p, []),
+    "dsd_kernel_launches": (ctypes.c_uint64, []),
     "dsd_set_wait_limit_ms": (_int, [_u32]),
     "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
@@ -104,6 +105,10 @@ def dsd_last_error():
 
 def dsd_version():
     return load().dsd_version().decode()
+
+
+def dsd_kernel_launches():
+    return int(load().dsd_kernel_launches())
 
 
 def dsd_set_wait_limit_ms(ms):

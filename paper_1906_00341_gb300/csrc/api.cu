@@ -2,6 +2,7 @@
 // output extraction kernels, profiling.
 #include "graph.cuh"
 
+#include <atomic>
 #include <new>
 #include <string.h>
 
@@ -10,6 +11,9 @@ const char* last_error();
 
 static uint64_t g_wait_ns = 20000ull * 1000000ull;
 uint64_t wait_limit_ns() { return g_wait_ns; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void prof_begin(dsd_graph* g, int phase) {
     if (!g->profiling) return;
@@ -182,7 +186,7 @@ dsd_status decompose(dsd_graph* g, int h) {
         g->prof_launches[kPhasePeel] = 2;
     }
     if (st == DSD_OK && n) {
-        k_map_u64<<<grid_for(n), 256, 0, s>>>(n, g->old_of, core_new, g->core);
+        k_map_u64<<<grid_for(n), 256, 0, s>>>(n, g->old_of, core_new, g->core); note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) st = cuda_fail(e, "map", __FILE__, __LINE__);
     }
@@ -190,6 +194,7 @@ dsd_status decompose(dsd_graph* g, int h) {
     dev_free(core_new, s);
     if (st != DSD_OK) return st;
     g->last_h = h;
+    g->prof_bytes[kPhasePeel] = pr.bytes;
     g->last_kmax = pr.kmax;
     g->last_mu = mu;
     g->nlevels = pr.nlevels;
@@ -217,10 +222,10 @@ dsd_status extract_set(dsd_graph* g, const uint64_t* core, const unsigned long l
     DSD_TRY(dalloc(&flags, (size_t)n + 1, s));
     dsd_status st = dalloc(&pos, (size_t)n + 1, s);
     if (st == DSD_OK) {
-        k_flags_ge<<<grid_for(n), 256, 0, s>>>(n, core, thr_dev, flags);
+        k_flags_ge<<<grid_for(n), 256, 0, s>>>(n, core, thr_dev, flags); note_launch();
         st = exclusive_scan_u32_to_u64(flags, pos, n, s);
         if (st == DSD_OK) {
-            k_compact<<<grid_for(n), 256, 0, s>>>(n, flags, pos, out_dev);
+            k_compact<<<grid_for(n), 256, 0, s>>>(n, flags, pos, out_dev); note_launch();
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) st = cuda_fail(e, "compact", __FILE__, __LINE__);
         }
@@ -297,6 +302,7 @@ const char* dsd_status_string(dsd_status s) {
 }
 
 const char* dsd_last_error(void) { return dsd::last_error(); }
+uint64_t dsd_kernel_launches(void) { return g_launches.load(); }
 const char* dsd_version(void) { return "libdsd 0.1 (sm_103a)"; }
 
 dsd_status dsd_set_wait_limit_ms(uint32_t ms) {
@@ -381,13 +387,13 @@ dsd_status dsd_graph_from_csr(uint32_t n, const uint64_t* off, const uint32_t* a
         if (e == cudaSuccess && total) e = cudaMemcpyAsync(buf + total, adj, total * 4, k, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, s);
         if (e == cudaSuccess && n) {
-            k_check_offsets<<<grid_for(n), 256, 0, s>>>(n, doff, total, err);
+            k_check_offsets<<<grid_for(n), 256, 0, s>>>(n, doff, total, err); note_launch();
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && !herr && n) {
-            k_expand_rows<<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, doff, buf);
+            k_expand_rows<<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, doff, buf); note_launch();
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) st = cuda_fail(e, "csr upload", __FILE__, __LINE__);
@@ -453,7 +459,7 @@ dsd_status dsd_degeneracy_order(dsd_graph* g, uint32_t* core2, uint32_t* rank,
             DSD_TRY(dalloc(&tmp, (size_t)n + 1, s));
             dst = tmp;
         }
-        if (n) k_u64_to_u32<<<grid_for(n), 256, 0, s>>>(n, g->core2, dst);
+        if (n) k_u64_to_u32<<<grid_for(n), 256, 0, s>>>(n, g->core2, dst); note_launch();
         DSD_LAUNCHED();
         if (tmp) {
             dsd_status st = copy_out(core2, tmp, (size_t)n * 4, mem, s);
@@ -490,7 +496,7 @@ dsd_status dsd_clique_degrees(dsd_graph* g, int h, uint64_t* deg, uint64_t* mu, 
     }
     if (st == DSD_OK && deg && n) {
         uint64_t* target = dout ? dout : deg;
-        k_map_u64<<<grid_for(n), 256, 0, s>>>(n, g->old_of, (const uint64_t*)dnew, target);
+        k_map_u64<<<grid_for(n), 256, 0, s>>>(n, g->old_of, (const uint64_t*)dnew, target); note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) st = cuda_fail(e, "map", __FILE__, __LINE__);
         if (st == DSD_OK && dout) st = copy_out(deg, dout, (size_t)n * 8, mem, s);
@@ -574,7 +580,7 @@ dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* dens
     DevResult hr;
     memset(&hr, 0, sizeof(hr));
     prof_begin(g, kPhaseExtract);
-    k_best_level<<<1, 1024, 0, s>>>(nl, lk, ls, lm, dr);
+    k_best_level<<<1, 1024, 0, s>>>(nl, lk, ls, lm, dr); note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_fail(e, "best level", __FILE__, __LINE__);
     if (st == DSD_OK && mem == DSD_MEM_HOST && (kmax_core || densest)) st = dalloc(&tmp, (size_t)n + 1, s);

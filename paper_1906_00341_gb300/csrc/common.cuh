@@ -49,6 +49,9 @@ constexpr uint32_t kNone = 0xffffffffu;
 // Process-wide wait limit for grid barriers (nanoseconds).
 uint64_t wait_limit_ns();
 
+// Process-wide count of kernel launches issued by the library.
+void note_launch();
+
 // --------------------------------------------------------- device utils
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

@@ -233,7 +233,7 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     DSD_CU(cudaMemsetAsync(mu_dev, 0, 8, s));
     if (n == 0) return DSD_OK;
     if (h == 2) {
-        k_degree_as_count<<<sms * 8, 256, 0, s>>>(n, g->roff, deg_new);
+        k_degree_as_count<<<sms * 8, 256, 0, s>>>(n, g->roff, deg_new); note_launch();
         DSD_LAUNCHED();
         unsigned long long m2 = g->m;
         DSD_CU(cudaMemcpyAsync(mu_dev, &m2, 8, cudaMemcpyHostToDevice, s));
@@ -257,13 +257,13 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     dsd_status st = DSD_OK;
     cudaError_t e = cudaMemsetAsync(A.cntML, 0, 8 * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
-        k_count_small<<<sms * 8, kCountThreads, 0, s>>>(A);
+        k_count_small<<<sms * 8, kCountThreads, 0, s>>>(A); note_launch();
         size_t smemM = (size_t)3 * kBitmapMax * 4 + (h >= 4 ? (size_t)kBitmapMax * 32 * 4 : 0);
         if (smemM > 48 * 1024)
             cudaFuncSetAttribute(k_count_medium, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smemM);
-        k_count_medium<<<sms * (h >= 4 ? 1 : 4), kCountThreads, smemM, s>>>(A);
-        if (h == 3) k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A);
+        k_count_medium<<<sms * (h >= 4 ? 1 : 4), kCountThreads, smemM, s>>>(A); note_launch();
+        if (h == 3) k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A); note_launch();
         e = cudaGetLastError();
     }
     uint32_t unsupported = 0;
@@ -287,7 +287,7 @@ dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out) {
     DSD_CU(cudaMemsetAsync(d, 0, 8, s));
     int sms = 152;
     num_sms(&sms);
-    k_count_bytes3<<<sms * 8, 256, 0, s>>>(g->n, g->roff, g->radj, g->rsplit, d);
+    k_count_bytes3<<<sms * 8, 256, 0, s>>>(g->n, g->roff, g->radj, g->rsplit, d); note_launch();
     unsigned long long h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

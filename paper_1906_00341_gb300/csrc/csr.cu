@@ -83,7 +83,7 @@ dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32
     CUSTEP(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
     CUSTEP(cudaMemsetAsync(err, 0, 4, s));
     if (m) {
-        k_count_endpoints<<<grid, 256, 0, s>>>(src, dst, m, n, cnt, err);
+        k_count_endpoints<<<grid, 256, 0, s>>>(src, dst, m, n, cnt, err); note_launch();
         CUSTEP(cudaGetLastError());
     }
     CUSTEP(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
@@ -99,7 +99,7 @@ dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32
     STEP(dalloc(&tmp2, total + 1, s));
     CUSTEP(cudaMemsetAsync(cnt, 0, ((size_t)n + 1) * 4, s));
     if (m) {
-        k_scatter<<<grid, 256, 0, s>>>(src, dst, m, n, pos, cnt, tmp);
+        k_scatter<<<grid, 256, 0, s>>>(src, dst, m, n, pos, cnt, tmp); note_launch();
         CUSTEP(cudaGetLastError());
     }
     // cnt now equals the per-row lengths again
@@ -112,7 +112,7 @@ dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32
         g->m = tot2 / 2;
         STEP(dalloc(&g->adj, tot2 + 1, s));
         if (n) {
-            k_copy_rows<<<grid, 256, 0, s>>>(tmp, pos, g->off, n, g->adj);
+            k_copy_rows<<<grid, 256, 0, s>>>(tmp, pos, g->off, n, g->adj); note_launch();
             CUSTEP(cudaGetLastError());
         }
     }

@@ -78,6 +78,7 @@ struct PeelResult {
     uint32_t nlevels = 0;
     uint32_t rounds = 0;
     uint64_t items = 0;       // frontier work items processed
+    uint64_t bytes = 0;       // metered algorithmic bytes
 };
 // off/adj/split: CSR in the working id space (split may be null for h = 2).
 // deg: [n] clique-degrees in, destroyed on return.  core/rnd: [n] outputs

@@ -128,7 +128,7 @@ dsd_status ensure_order(dsd_graph* g) {
     }
     // K2: edge core numbers and removal rounds
     prof_begin(g, kPhaseOrderPeel);
-    k_row_lengths<<<grid, 256, 0, s>>>(n, g->off, deg);
+    k_row_lengths<<<grid, 256, 0, s>>>(n, g->off, deg); note_launch();
     CUSTEP(cudaGetLastError());
     STEP(run_peel(g, 2, n, g->off, g->adj, nullptr, 0, deg, g->m, g->core2, g->rnd, g->lvl2_k,
                   g->lvl2_size, g->lvl2_mu, &pr));
@@ -137,7 +137,7 @@ dsd_status ensure_order(dsd_graph* g) {
     g->degeneracy = (uint32_t)pr.kmax;
     g->order_kmax = pr.kmax;
     g->nlevels2 = pr.nlevels;
-    g->prof_bytes[kPhaseOrderPeel] = 0;
+    g->prof_bytes[kPhaseOrderPeel] = pr.bytes;
     R = pr.rounds + 1;
 
     // K3: rank by (round, id), relabel, rebuild rows
@@ -149,18 +149,18 @@ dsd_status ensure_order(dsd_graph* g) {
     STEP(dalloc(&tmp, (2 * g->m > n ? 2 * g->m : (uint64_t)n) + 1, s));
     STEP(dalloc(&dmax, 1, s));
     CUSTEP(cudaMemsetAsync(hist, 0, ((size_t)R + 1) * 4, s));
-    k_round_hist<<<grid, 256, 0, s>>>(n, g->rnd, hist);
+    k_round_hist<<<grid, 256, 0, s>>>(n, g->rnd, hist); note_launch();
     CUSTEP(cudaGetLastError());
     STEP(exclusive_scan_u32_to_u64(hist, start, R, s));
     CUSTEP(cudaMemsetAsync(rdeg, 0, ((size_t)n + 1) * 4, s));
-    k_round_scatter<<<grid, 256, 0, s>>>(n, g->rnd, start, rdeg, g->old_of);
+    k_round_scatter<<<grid, 256, 0, s>>>(n, g->rnd, start, rdeg, g->old_of); note_launch();
     CUSTEP(cudaGetLastError());
     // rows = rounds; sort the members of each round by id (distinct ids)
     STEP(segmented_sort_unique(g->old_of, tmp, start, hist, rdeg, R, n, s));
-    k_invert<<<grid, 256, 0, s>>>(n, g->old_of, g->new_of, g->off, rdeg);
+    k_invert<<<grid, 256, 0, s>>>(n, g->old_of, g->new_of, g->off, rdeg); note_launch();
     CUSTEP(cudaGetLastError());
     STEP(exclusive_scan_u32_to_u64(rdeg, g->roff, n, s));
-    k_fill_rows<<<grid, 256, 0, s>>>(n, g->old_of, g->new_of, g->off, g->adj, g->roff, g->radj);
+    k_fill_rows<<<grid, 256, 0, s>>>(n, g->old_of, g->new_of, g->off, g->adj, g->roff, g->radj); note_launch();
     CUSTEP(cudaGetLastError());
     {
         // rows have distinct entries; reuse hist as the (ignored) unique counts
@@ -171,7 +171,7 @@ dsd_status ensure_order(dsd_graph* g) {
         if (st != DSD_OK) goto done;
     }
     CUSTEP(cudaMemsetAsync(dmax, 0, 4, s));
-    k_split<<<grid, 256, 0, s>>>(n, g->roff, g->radj, g->rsplit, dmax);
+    k_split<<<grid, 256, 0, s>>>(n, g->roff, g->radj, g->rsplit, dmax); note_launch();
     CUSTEP(cudaGetLastError());
     CUSTEP(cudaMemcpyAsync(&hmax, dmax, 4, cudaMemcpyDeviceToHost, s));
     CUSTEP(cudaStreamSynchronize(s));

@@ -53,7 +53,16 @@ struct PeelCtrl {
     uint32_t nlevels;
     uint32_t rounds;
     unsigned long long items;
+    unsigned long long bytes;   // algorithmic bytes (see meter notes below)
 };
+
+// Byte meter.  Every global-memory element the algorithm reads or writes is
+// counted once per access: ids 4 B, offsets 8 B, state 1 B, counters 8 B, an
+// atomic read-modify-write 16 B, a binary search over a row of d entries
+// floor(log2 d) + 1 probes of 4 B.  Shared-memory traffic is not counted.
+__device__ __forceinline__ unsigned probes(uint64_t d) {
+    return d ? 64u - (unsigned)__clzll((long long)d) : 0u;
+}
 
 struct PeelParams {
     uint32_t n;
@@ -80,6 +89,7 @@ struct PeelParams {
 
 // ------------------------------------------------------------ barrier
 __device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns) {
+    __shared__ uint32_t s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile uint32_t* genp = &c->bar_gen;
@@ -102,9 +112,11 @@ __device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns) {
             }
         }
         __threadfence();
+        s_err = *(volatile uint32_t*)&c->error;
     }
     __syncthreads();
-    return *(volatile uint32_t*)&c->error == 0;
+    // one decision per block, so that its threads leave (or stay) together
+    return s_err == 0;
 }
 
 // ------------------------------------------------------------ helpers
@@ -192,13 +204,17 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
 // smallest such member is w.  Executed by one warp.
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
-                           uint32_t* rows, uint32_t* big_cnt, unsigned long long& destroyed) {
+                           uint32_t* rows, uint32_t* big_cnt, unsigned long long& destroyed,
+                           unsigned long long& bytes) {
     unsigned lane = lane_id();
     uint8_t sw = P.state[w];
+    if (lane == 0) bytes += 4 + 1;   // w, state[w]
     if (!(sw == kAlive || (sw == kFront && w > v))) return;
     const uint32_t* Nv = P.adj + P.off[v];
     uint64_t dv = P.off[v + 1] - P.off[v];
     uint64_t b = P.split[w], e = P.off[w + 1];
+    if (lane == 0) bytes += 16;
+    const unsigned pr = probes(dv);
     uint32_t nc = 0;
     for (uint64_t p0 = b; p0 < e; p0 += 32) {
         uint64_t p = p0 + lane;
@@ -206,9 +222,11 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         uint32_t x = 0;
         if (p < e) {
             x = P.adj[p];
+            bytes += 4 + 1;
             if (candidate(P, x, v)) {
                 uint64_t pos = lower_bound_u32(Nv, dv, x);
                 ok = pos < dv && Nv[pos] == x;
+                bytes += 4ull * pr;
             }
         }
         unsigned bal = __ballot_sync(0xffffffffu, ok);
@@ -222,7 +240,11 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         tot = nc;
         for (uint32_t i = lane; i < nc; i += 32) {
             uint32_t x = C[i];
-            if (P.state[x] == kAlive) dec_and_queue(P, x, 1ull, k, next, next_cnt);
+            bytes += 1;
+            if (P.state[x] == kAlive) {
+                dec_and_queue(P, x, 1ull, k, next, next_cnt);
+                bytes += 16;
+            }
         }
     } else {
         if (nc < (uint32_t)r) return;
@@ -242,8 +264,10 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
                 uint32_t x = C[i];
                 uint64_t xb = P.split[x], xe = P.off[x + 1];
                 unsigned hits = 0;
+                if (lane == 0) bytes += 16;
                 for (uint64_t p = xb + lane; p < xe; p += 32) {
                     uint32_t y = P.adj[p];
+                    bytes += 4;
                     uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
                     if (pos < nc && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
                 }
@@ -252,6 +276,9 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
                 tot += hits;
             }
         } else {
+            if (lane == 0)
+                for (uint32_t i = 0; i < nc; i++)
+                    bytes += 16 + 4ull * (P.off[C[i] + 1] - P.split[C[i]]);
             warp_build_rows32(C, nc, P.off, P.adj, P.split, rows);
             tot = warp_dfs32(rows, nc, r, cnt);
         }
@@ -259,13 +286,21 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         if (tot)
             for (uint32_t i = lane; i < nc; i += 32) {
                 uint32_t x = C[i];
-                if (cnt[i] && P.state[x] == kAlive)
-                    dec_and_queue(P, x, (unsigned long long)cnt[i], k, next, next_cnt);
+                if (cnt[i]) {
+                    bytes += 1;
+                    if (P.state[x] == kAlive) {
+                        dec_and_queue(P, x, (unsigned long long)cnt[i], k, next, next_cnt);
+                        bytes += 16;
+                    }
+                }
             }
         __syncwarp();
     }
     if (tot && lane == 0) {
-        if (sw == kAlive) dec_and_queue(P, w, tot, k, next, next_cnt);
+        if (sw == kAlive) {
+            dec_and_queue(P, w, tot, k, next, next_cnt);
+            bytes += 16;
+        }
         destroyed += tot;
     }
 }
@@ -349,6 +384,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
     int ap = 0;
     uint32_t alive_cnt = P.n;
     unsigned long long items = 0;
+    unsigned long long bytes = 0;
 
     for (;;) {
         // ---------------------------------------------------------- P1
@@ -359,10 +395,14 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
             P.state[v] = kGone;
             P.core[v] = k;
             if (P.rnd) P.rnd[v] = r - 1;
+            bytes += 4 + 1 + 8 + (P.rnd ? 4 : 0);
         }
         uint32_t fcur = c->fcnt[r % 3];
         uint32_t* Fcur = P.front[r % 3];
-        for (uint64_t i = gtid; i < fcur; i += gthreads) P.state[Fcur[i]] = kFront;
+        for (uint64_t i = gtid; i < fcur; i += gthreads) {
+            P.state[Fcur[i]] = kFront;
+            bytes += 4 + 1;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             if (r) {
                 mu_alive -= c->destroyed[(r + 2) % 3];
@@ -384,10 +424,12 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                 uint32_t v = 0;
                 if (i < alive_cnt) {
                     v = Ain[i];
+                    bytes += 4 + 1;
                     if (P.state[v] != kGone) {
                         keep = true;
                         unsigned long long d = P.deg[v];
                         mn = d < mn ? d : mn;
+                        bytes += 8 + 4;
                     }
                 }
                 warp_append(keep, v, &c->new_alive[jumps & 1], Aout);
@@ -416,9 +458,11 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                 uint32_t v = 0;
                 if (i < na) {
                     v = Aout[i];
+                    bytes += 4 + 8;
                     if (P.deg[v] <= k) {
                         in = true;
                         P.state[v] = kFront;
+                        bytes += 1 + 4;
                     }
                 }
                 warp_append(in, v, &c->fcnt[r % 3], Fcur);
@@ -435,7 +479,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
             // flatten (v, neighbour index) items over the whole grid
             block_prefix_degrees(P, Fcur, fcur, s_pre, s_red);
             unsigned long long T = s_pre[fcur];
-            items += T;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                items += T;
+                bytes += 20ull * fcur;   // frontier ids and their offsets
+            }
             if (P.h == 2) {
                 for (uint64_t t = gtid; t < T; t += gthreads) {
                     uint32_t lo = 0, hi = fcur;  // last i with s_pre[i] <= t
@@ -446,9 +493,11 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                     uint32_t v = Fcur[lo];
                     uint32_t u = P.adj[P.off[v] + (t - s_pre[lo])];
                     uint8_t su = P.state[u];
+                    bytes += 4 + 1;
                     if (su == kAlive) {
                         dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
                         destroyed++;
+                        bytes += 16;
                     } else if (su == kFront && u > v) {
                         destroyed++;
                     }
@@ -463,7 +512,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                     uint32_t v = Fcur[lo];
                     uint32_t w = P.adj[P.off[v] + (t - s_pre[lo])];
                     process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows,
-                               &c->big_cnt[r % 3], destroyed);
+                               &c->big_cnt[r % 3], destroyed, bytes);
                 }
             }
         } else {
@@ -474,14 +523,19 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                     for (uint64_t p = b + lane; p < e; p += 32) {
                         uint32_t u = P.adj[p];
                         uint8_t su = P.state[u];
+                        bytes += 4 + 1;
                         if (su == kAlive) {
                             dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
                             destroyed++;
+                            bytes += 16;
                         } else if (su == kFront && u > v) {
                             destroyed++;
                         }
                     }
-                    if (lane == 0) items += e - b;
+                    if (lane == 0) {
+                        items += e - b;
+                        bytes += 20;
+                    }
                 }
             } else {
                 for (uint64_t i = blockIdx.x; i < fcur; i += gridDim.x) {
@@ -489,8 +543,11 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
                     uint64_t b = P.off[v], e = P.off[v + 1];
                     for (uint64_t p = b + wid; p < e; p += kPeelWarps)
                         process_vw(P, v, P.adj[p], k, Fnext, next_cnt, wC, wCnt, wRows,
-                                   &c->big_cnt[r % 3], destroyed);
-                    if (threadIdx.x == 0) items += e - b;
+                                   &c->big_cnt[r % 3], destroyed, bytes);
+                    if (threadIdx.x == 0) {
+                        items += e - b;
+                        bytes += 20;
+                    }
                 }
             }
         }
@@ -519,7 +576,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
         c->nlevels = nlev;
         c->rounds = r;
     }
+    items = warp_sum(items);
+    bytes = warp_sum(bytes);
     if (lane == 0 && items) atomicAdd(&c->items, items);
+    if (lane == 0 && bytes) atomicAdd(&c->bytes, bytes);
 }
 
 __global__ void k_peel_init(uint32_t n, uint8_t* state, uint32_t* alive0, PeelCtrl* c) {
@@ -609,13 +669,14 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.ctrl = ctrl;
     e = cudaMemsetAsync(ctrl, 0, sizeof(PeelCtrl), s);
     if (e == cudaSuccess) {
-        k_peel_init<<<sms * 4, 256, 0, s>>>(n, state, P.alive[0], ctrl);
+        k_peel_init<<<sms * 4, 256, 0, s>>>(n, state, P.alive[0], ctrl); note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         void* args[] = {&P};
         e = cudaLaunchCooperativeKernel((void*)k_peel, dim3(grid), dim3(kPeelThreads), args,
                                         smem, s);
+        note_launch();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(PeelCtrl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -638,6 +699,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     res->nlevels = hc.nlevels;
     res->rounds = hc.rounds;
     res->items = hc.items;
+    res->bytes = hc.bytes;
 done:
     dev_free(state, s);
     dev_free(lists, s);

@@ -151,9 +151,9 @@ dsd_status exclusive_scan_impl(const T* in, uint64_t* out, uint64_t n, cudaStrea
     }
     uint64_t* sums = nullptr;
     DSD_TRY(dalloc(&sums, nt + 1, s));
-    k_tile_sums<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums);
-    k_scan_sums<<<1, 1024, 0, s>>>(sums, nt);
-    k_scan_apply<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums, out);
+    k_tile_sums<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums); note_launch();
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nt); note_launch();
+    k_scan_apply<T><<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, sums, out); note_launch();
     cudaError_t e = cudaGetLastError();
     dev_free(sums, s);
     if (e != cudaSuccess) return cuda_fail(e, "scan launch", __FILE__, __LINE__);
@@ -375,10 +375,10 @@ dsd_status segmented_sort_unique(uint32_t* vals, uint32_t* tmp, const uint64_t* 
     cudaError_t e = cudaMemsetAsync(cnt, 0, kClasses * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         unsigned g = (unsigned)((rows + 255) / 256);
-        k_classify<<<g < 65535u ? g : 65535u, 256, 0, s>>>(len, rows, L);
-        k_sort_small<<<sms * 8, 256, 0, s>>>(vals, pos, len, newlen, L.rows[0], cnt + 0);
+        k_classify<<<g < 65535u ? g : 65535u, 256, 0, s>>>(len, rows, L); note_launch();
+        k_sort_small<<<sms * 8, 256, 0, s>>>(vals, pos, len, newlen, L.rows[0], cnt + 0); note_launch();
         k_sort_block<kMedMax><<<sms * 4, 256, kMedMax * 4, s>>>(vals, pos, len, newlen,
-                                                                  L.rows[1], cnt + 1);
+                                                                  L.rows[1], cnt + 1); note_launch();
         static bool attr_done = false;
         if (!attr_done) {
             cudaFuncSetAttribute(k_sort_block<kLargeMax>,
@@ -388,9 +388,9 @@ dsd_status segmented_sort_unique(uint32_t* vals, uint32_t* tmp, const uint64_t* 
             attr_done = true;
         }
         k_sort_block<kLargeMax><<<sms * 2, 1024, kLargeMax * 4, s>>>(vals, pos, len, newlen,
-                                                                      L.rows[2], cnt + 2);
+                                                                      L.rows[2], cnt + 2); note_launch();
         k_sort_huge<<<sms, 1024, kLargeMax * 4, s>>>(vals, tmp, pos, len, newlen, L.rows[3],
-                                                     cnt + 3);
+                                                     cnt + 3); note_launch();
         e = cudaGetLastError();
     }
     dev_free(lists, s);
