@@ -174,6 +174,29 @@ typedef struct {
 dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
                         int mem, dsd_core_app_result* r);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory (a host framework whose allocator already
+ * holds the device's memory, or a serving path that may not allocate in the
+ * middle of a request).  It computes what dsd_clique_degrees computes for
+ * h = 3 (triangle clique-degrees deg[v] and mu), directly from a caller CSR,
+ * without a graph handle and without allocating anything.
+ *   off: device pointer, n+1 entries; adj: device pointer, off[n] entries.
+ *        The CSR must already be symmetric with ascending, duplicate-free
+ *        rows and no self-loops (e.g. the output of dsd_graph_csr).
+ *   deg: device pointer, n entries (written); mu: device pointer (written).
+ *   cuda_stream: the stream the work is ordered on (NULL = legacy stream).
+ * Its scratch is a fixed 4 MiB __device__ array that every GPU which loads
+ * the library keeps until the process exits; n must not exceed 1,048,512
+ * (DSD_ERR_UNSUPPORTED otherwise).  The first call on a device looks up that
+ * array's address and caches it: make it before any stream capture begins.
+ * All calls on a device share the array, so calls that overlap on the GPU
+ * (other streams, other threads) race: serialise them.  Returns once the
+ * work is queued; synchronise the stream before reading deg and mu. */
+dsd_status dsd_triangle_degrees_noalloc(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                                        uint64_t* deg, uint64_t* mu, void* cuda_stream);
+
 /* ---------------------------------------------------------- profiling */
 
 /* Per-phase device timings (CUDA events on the graph's stream) of the most

@@ -65,6 +65,7 @@ SIGNATURES = {
     "dsd_core_decompose": (_int, [_P, _int, _P, _P, _int]),
     "dsd_level_stats": (_int, [_P, _int, _P, _P, _P, _u32, _P, _int]),
     "dsd_core_app": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult)]),
+    "dsd_triangle_degrees_noalloc": (_int, [_u32, _P, _P, _P, _P, _P]),
     "dsd_set_profiling": (_int, [_P, _int]),
     "dsd_phase_stats": (_int, [_P, _P, _P, _P]),
 }
@@ -166,6 +167,10 @@ def dsd_core_app(g, h, kcore_ptr, densest_ptr, mem):
     r = CoreAppResult()
     _check(load().dsd_core_app(g, h, kcore_ptr, densest_ptr, mem, ctypes.byref(r)))
     return r
+
+
+def dsd_triangle_degrees_noalloc(n, off_ptr, adj_ptr, deg_ptr, mu_ptr, stream_ptr):
+    _check(load().dsd_triangle_degrees_noalloc(n, off_ptr, adj_ptr, deg_ptr, mu_ptr, stream_ptr))
 
 
 def dsd_set_profiling(g, on):
