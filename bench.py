@@ -154,8 +154,8 @@ def run_ours(args, rank, world, local):
     hnd = L.dsd_graph_from_edges(n, m_draws, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE, sp)
     L.dsd_set_profiling(hnd, True)
     r0 = L.dsd_core_app(hnd, h, kcore.data_ptr(), dens.data_ptr(), L.DSD_MEM_DEVICE)
-    phase = L.Graph.__new__(L.Graph)
     ms, by, la = L.dsd_phase_stats(hnd)
+    pstats = {"degeneracy_peel": L.dsd_peel_stats(hnd, 0), "kpsi_peel": L.dsd_peel_stats(hnd, 1)}
     n_, m_und = L.dsd_graph_info(hnd)
     mu = None
     deg_mu = np.zeros(1, np.uint64)
@@ -258,6 +258,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clocks,
+        "peel_stats": pstats,
     }
     return line, (n, s, d, h, mu)
 

@@ -78,6 +78,13 @@ uint64_t dsd_kernel_launches(void);
  * Default 20000 ms.  Applies to calls started afterwards, process-wide. */
 dsd_status dsd_set_wait_limit_ms(uint32_t ms);
 
+/* Tuning: once at most `max_alive` vertices remain alive, the peeling kernel
+ * keeps the alive list and the frontier in every block's shared memory and
+ * needs one grid barrier per round (the tail of many tiny levels).  Default
+ * 16384 (also capped by shared memory); 0 disables it.  Results do not
+ * depend on it.  Process-wide; applies to calls started afterwards. */
+dsd_status dsd_set_peel_small_limit(uint32_t max_alive);
+
 /* ---------------------------------------------------------------- graphs */
 
 /* Build a graph from an edge list (Sec. 2 data model).  Edge i joins
@@ -209,6 +216,18 @@ dsd_status dsd_triangle_degrees_noalloc(uint32_t n, const uint64_t* off, const u
 #define DSD_NPHASES 6
 dsd_status dsd_set_profiling(dsd_graph* g, int on);
 dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* launches);
+
+/* Counters of the last peeling run: which = 0 the degeneracy (h = 2) peel,
+ * 1 the last (k,Psi) peel with h >= 3.  out[DSD_PEEL_STATS] receives:
+ * rounds, levels, frontier work items, metered algorithmic bytes, time block 0
+ * spent inside grid barriers (ns), barriers passed, row compactions, block
+ * size, grid size, k_max, first round run with the alive set replicated in
+ * every block's shared memory (0 if none), then block 0's time (ns) in each
+ * phase outside barriers: [large regime] retire/mark, alive-list scan, level
+ * jump, clique enumeration; [small regime] retire/copy, level jump,
+ * mark/bitmaps, clique enumeration.  Zeros if that peel has not run. */
+#define DSD_PEEL_STATS 19
+dsd_status dsd_peel_stats(dsd_graph* g, int which, uint64_t* out);
 
 #ifdef __cplusplus
 }

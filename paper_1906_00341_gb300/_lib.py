@@ -54,6 +54,7 @@ SIGNATURES = {
     "dsd_version": (ctypes.c_char_p, []),
     "dsd_kernel_launches": (ctypes.c_uint64, []),
     "dsd_set_wait_limit_ms": (_int, [_u32]),
+    "dsd_set_peel_small_limit": (_int, [_u32]),
     "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_destroy": (None, [_P]),
@@ -68,7 +69,13 @@ SIGNATURES = {
     "dsd_triangle_degrees_noalloc": (_int, [_u32, _P, _P, _P, _P, _P]),
     "dsd_set_profiling": (_int, [_P, _int]),
     "dsd_phase_stats": (_int, [_P, _P, _P, _P]),
+    "dsd_peel_stats": (_int, [_P, _int, _P]),
 }
+
+PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
+              "threads", "grid", "kmax", "small_round",
+              "t_large_retire", "t_large_scan", "t_large_jump", "t_large_enum",
+              "t_small_retire", "t_small_jump", "t_small_mark", "t_small_enum")
 
 
 def load(path: str = LIB_PATH):
@@ -114,6 +121,10 @@ def dsd_kernel_launches():
 
 def dsd_set_wait_limit_ms(ms):
     _check(load().dsd_set_wait_limit_ms(ms))
+
+
+def dsd_set_peel_small_limit(max_alive):
+    _check(load().dsd_set_peel_small_limit(max_alive))
 
 
 def dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr):
@@ -184,6 +195,12 @@ def dsd_phase_stats(g):
     _check(load().dsd_phase_stats(g, ctypes.addressof(ms), ctypes.addressof(by),
                                   ctypes.addressof(la)))
     return list(ms), list(by), list(la)
+
+
+def dsd_peel_stats(g, which):
+    out = (ctypes.c_uint64 * len(PEEL_STATS))()
+    _check(load().dsd_peel_stats(g, which, ctypes.addressof(out)))
+    return dict(zip(PEEL_STATS, [int(x) for x in out]))
 
 
 # -------------------------------------------------------- convenience

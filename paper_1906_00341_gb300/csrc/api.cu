@@ -12,8 +12,27 @@ const char* last_error();
 static uint64_t g_wait_ns = 20000ull * 1000000ull;
 uint64_t wait_limit_ns() { return g_wait_ns; }
 
+static std::atomic<uint32_t> g_small_limit{16384};
+uint32_t peel_small_limit() { return g_small_limit.load(); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void record_peel(dsd_graph* g, int which, const PeelResult& r) {
+    uint64_t* o = g->peel_stats[which];
+    o[0] = r.rounds;
+    o[1] = r.nlevels;
+    o[2] = r.items;
+    o[3] = r.bytes;
+    o[4] = r.barrier_ns;
+    o[5] = r.barriers;
+    o[6] = r.compactions;
+    o[7] = r.threads;
+    o[8] = r.grid;
+    o[9] = r.kmax;
+    o[10] = r.small_round;
+    for (int i = 0; i < 8; i++) o[11 + i] = r.tph[i];
+}
 
 void prof_begin(dsd_graph* g, int phase) {
     if (!g->profiling) return;
@@ -195,6 +214,7 @@ dsd_status decompose(dsd_graph* g, int h) {
     if (st != DSD_OK) return st;
     g->last_h = h;
     g->prof_bytes[kPhasePeel] = pr.bytes;
+    record_peel(g, 1, pr);
     g->last_kmax = pr.kmax;
     g->last_mu = mu;
     g->nlevels = pr.nlevels;
@@ -311,6 +331,11 @@ dsd_status dsd_set_wait_limit_ms(uint32_t ms) {
         return DSD_ERR_INVALID;
     }
     g_wait_ns = (uint64_t)ms * 1000000ull;
+    return DSD_OK;
+}
+
+dsd_status dsd_set_peel_small_limit(uint32_t max_alive) {
+    g_small_limit = max_alive;
     return DSD_OK;
 }
 
@@ -624,6 +649,16 @@ dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* dens
     r->densest_mu = hr.densest_mu;
     r->nlevels = hr.nlevels;
     r->reserved = 0;
+    return DSD_OK;
+}
+
+dsd_status dsd_peel_stats(dsd_graph* g, int which, uint64_t* out) {
+    DSD_TRY(check_graph(g));
+    if (!out || (which != 0 && which != 1)) {
+        set_error("dsd_peel_stats: which must be 0 or 1 and out non-NULL");
+        return DSD_ERR_INVALID;
+    }
+    for (int i = 0; i < DSD_PEEL_STATS; i++) out[i] = g->peel_stats[which][i];
     return DSD_OK;
 }
 

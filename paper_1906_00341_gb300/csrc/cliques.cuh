@@ -23,17 +23,18 @@ constexpr uint32_t kBitmapMax = 1024;   // candidates per bitmap problem
 
 // ---------------------------------------------------------------------------
 // Row construction: for candidate i, the positions j > i whose vertex is in
-// N+(C[i]).  Candidates are sorted ascending, N+ lists too, and every j > i
-// automatically has C[j] > C[i]; membership is a binary search in C.
+// N+(C[i]) = adj[nb[x] .. ne[x]).  Candidates are sorted ascending, N+ lists
+// too, and every j > i automatically has C[j] > C[i]; membership is a binary
+// search in C.
 
 // Warp builds one-word rows for |C| <= 32 (rows[i] for i < nc).
 __device__ __forceinline__ void warp_build_rows32(const uint32_t* C, uint32_t nc,
-                                                  const uint64_t* off, const uint32_t* adj,
-                                                  const uint64_t* split, uint32_t* rows) {
+                                                  const uint64_t* ne, const uint32_t* adj,
+                                                  const uint64_t* nb, uint32_t* rows) {
     unsigned lane = lane_id();
     for (uint32_t i = 0; i < nc; i++) {
         uint32_t x = C[i];
-        uint64_t b = split[x], e = off[x + 1];
+        uint64_t b = nb[x], e = ne[x];
         uint32_t bits = 0;
         for (uint64_t p = b + lane; p - lane < e; p += 32) {
             bool hit = false;
@@ -104,13 +105,13 @@ __device__ __forceinline__ unsigned long long warp_dfs32(const uint32_t* rows, u
 // Block-level bitmap routines for 32 < |C| <= 1024.  rows: nc * W words in
 // shared memory (W = ceil(nc/32)), zeroed by the caller.
 __device__ __forceinline__ void block_build_rows(const uint32_t* C, uint32_t nc, uint32_t W,
-                                                 const uint64_t* off, const uint32_t* adj,
-                                                 const uint64_t* split, uint32_t* rows) {
+                                                 const uint64_t* ne, const uint32_t* adj,
+                                                 const uint64_t* nb, uint32_t* rows) {
     unsigned lane = lane_id();
     unsigned nw = blockDim.x >> 5;
     for (uint32_t i = warp_id(); i < nc; i += nw) {
         uint32_t x = C[i];
-        uint64_t b = split[x], e = off[x + 1];
+        uint64_t b = nb[x], e = ne[x];
         for (uint64_t p = b + lane; p < e; p += 32) {
             uint32_t y = adj[p];
             uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);

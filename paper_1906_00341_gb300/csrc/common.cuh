@@ -52,6 +52,9 @@ uint64_t wait_limit_ns();
 // Process-wide count of kernel launches issued by the library.
 void note_launch();
 
+// Largest alive set the peel replicates in every block's shared memory.
+uint32_t peel_small_limit();
+
 // --------------------------------------------------------- device utils
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_small(CountArgs A) {
                 }
                 tot = t;
             } else {
-                warp_build_rows32(C, d, A.off, A.adj, A.split, rows);
+                warp_build_rows32(C, d, A.off + 1, A.adj, A.split, rows);
                 tot = warp_dfs32(rows, d, A.r, cnt);
             }
             __syncwarp();
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kCountThreads) k_count_medium(CountArgs A) {
                 if (lane == 0) mine += hits;
             }
         } else {
-            block_build_rows(C, d, W, A.off, A.adj, A.split, rows);
+            block_build_rows(C, d, W, A.off + 1, A.adj, A.split, rows);
             __syncthreads();
             mine = block_dfs(rows, d, W, A.r, cnt);
         }

@@ -51,6 +51,9 @@ struct dsd_graph {
     uint32_t* lvl_size = nullptr;
     uint64_t* lvl_mu = nullptr;
 
+    // peel statistics: [0] degeneracy peel, [1] last (k,Psi) peel
+    uint64_t peel_stats[2][DSD_PEEL_STATS] = {};
+
     // profiling
     bool profiling = false;
     cudaEvent_t ev[2 * 6] = {};
@@ -79,6 +82,13 @@ struct PeelResult {
     uint32_t rounds = 0;
     uint64_t items = 0;       // frontier work items processed
     uint64_t bytes = 0;       // metered algorithmic bytes
+    uint64_t barrier_ns = 0;  // time block 0 spent in grid barriers
+    uint32_t barriers = 0;
+    uint32_t compactions = 0;
+    uint32_t threads = 0;     // block size used
+    uint32_t grid = 0;        // blocks launched
+    uint32_t small_round = 0; // first round of the small regime (0 = never)
+    uint64_t tph[8] = {};     // block 0's time per phase (ns)
 };
 // off/adj/split: CSR in the working id space (split may be null for h = 2).
 // deg: [n] clique-degrees in, destroyed on return.  core/rnd: [n] outputs
@@ -87,6 +97,9 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
                     const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
                     uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
                     uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res);
+
+// Statistics of the last peel runs: [0] degeneracy peel, [1] (k,Psi) peel.
+void record_peel(dsd_graph* g, int which, const PeelResult& r);
 
 // Profiling helpers.
 void prof_begin(dsd_graph* g, int phase);

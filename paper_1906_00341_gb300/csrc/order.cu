@@ -138,6 +138,7 @@ dsd_status ensure_order(dsd_graph* g) {
     g->order_kmax = pr.kmax;
     g->nlevels2 = pr.nlevels;
     g->prof_bytes[kPhaseOrderPeel] = pr.bytes;
+    record_peel(g, 0, pr);
     R = pr.rounds + 1;
 
     // K3: rank by (round, id), relabel, rebuild rows

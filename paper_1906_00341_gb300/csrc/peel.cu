@@ -13,28 +13,53 @@
 // recorded: these give the CoreApp outputs (the k_max core, Lemma 6) and the
 // densest residual level (Pruning1, Sec. 5.1) without storing cliques.
 //
-// One persistent cooperative kernel runs every round; the phases of a round
-// are separated by grid barriers whose waits are bounded in time (a wait that
-// runs out records DSD_ERR_TIMEOUT and every block leaves).
+// One persistent cooperative kernel runs every round; phases are separated
+// by grid barriers whose waits are bounded in time (a wait that runs out
+// records DSD_ERR_TIMEOUT and every block leaves).
 //
-// Round r (F_r = frontier of round r, lists indexed r mod 3):
+// Large regime (many alive vertices), round r, F_r in global lists r mod 3:
 //   P1  mark F_{r-1} removed (core = k); mark F_r as frontier     | barrier
 //   J   (only if F_r is empty) compact the alive list and take   |
 //       the minimum count; k = that minimum; record the level    | barrier
-//       (k, |R_k|, mu(R_k)); F_r = alive vertices with count <= k | barrier
+//       (k, |R_k|, mu(R_k)); F_r = alive vertices with count <= k;|
+//       when the alive set has halved, drop removed vertices     |
+//       from the rows of alive vertices                          | barrier
 //   P2  enumerate the cliques each v in F_r destroys; decrement   | barrier
 //   P2b (h >= 5) candidate sets above 32 vertices, one block each | barrier
+//
+// Small regime (the long tail of tiny levels: at most `asmall` vertices
+// alive).  Every block holds a slice of the alive list and the whole
+// frontier in shared memory and performs the bookkeeping of P1 itself
+// (identical writes in every block).  A level jump is distributed: each block
+// publishes its slice minimum and the slice vertices attaining it; after one
+// barrier every block combines them into k and the frontier.  So a round
+// needs one grid barrier after P2, plus the jump barrier (no block may
+// decrement counts another block is still reading) and one when big items
+// exist.  On entry every alive vertex gets a fixed local id, kept in the
+// upper bits of its state word; each block then holds, for the first
+// frontier vertices, a bitmap over local ids of their neighbourhoods, so that
+// "x in N(v)" is one shared-memory bit instead of a binary search in global
+// memory.
+//
+// Rows live in a private copy of the oriented CSR: row v is
+// wadj[off[v] .. wend[v]) and N+(v) = wadj[wnb[v] .. wend[v]).  Compaction
+// rewrites a row in place (stable, so rows stay sorted) and moves wend/wnb.
 #include "cliques.cuh"
 #include "graph.cuh"
+
+#include <string.h>
 
 namespace dsd {
 namespace {
 
-enum : uint8_t { kAlive = 0, kFront = 1, kGone = 2 };
+// state word: bits 0-1 the state, bits 2-31 the local id (small regime)
+enum : uint32_t { kAlive = 0, kFront = 1, kGone = 2 };
 enum : uint32_t { kErrTimeout = 1, kErrBigOverflow = 2 };
-constexpr int kPeelThreads = 256;
-constexpr int kPeelWarps = kPeelThreads / 32;
 constexpr uint32_t kSmallFront = 1024;
+constexpr uint32_t kBitmapSlots = 16;   // frontier vertices with a shared bitmap
+constexpr int kChunks = 4;              // 32-entry chunks of a row in flight per warp
+
+__device__ __forceinline__ uint32_t st_of(uint32_t w) { return w & 3u; }
 
 struct PeelCtrl {
     unsigned long long min_deg[2];
@@ -53,13 +78,21 @@ struct PeelCtrl {
     uint32_t nlevels;
     uint32_t rounds;
     unsigned long long items;
-    unsigned long long bytes;   // algorithmic bytes (see meter notes below)
+    unsigned long long bytes;       // algorithmic bytes (meter notes below)
+    unsigned long long barrier_ns;  // block 0's time inside grid barriers
+    uint32_t barriers;
+    uint32_t compactions;
+    uint32_t small_round;           // first round of the small regime (0 = never)
+    uint32_t pad3;
+    unsigned long long tph[8];      // block 0's time per phase (ns)
 };
 
 // Byte meter.  Every global-memory element the algorithm reads or writes is
-// counted once per access: ids 4 B, offsets 8 B, state 1 B, counters 8 B, an
-// atomic read-modify-write 16 B, a binary search over a row of d entries
-// floor(log2 d) + 1 probes of 4 B.  Shared-memory traffic is not counted.
+// counted once per access: ids and state words 4 B, offsets 8 B, counters
+// 8 B, an atomic read-modify-write 16 B, a binary search over a row of d
+// entries floor(log2 d) + 1 probes of 4 B.  Shared-memory traffic is not
+// counted, and bookkeeping that every block repeats in the small regime
+// counts once.
 __device__ __forceinline__ unsigned probes(uint64_t d) {
     return d ? 64u - (unsigned)__clzll((long long)d) : 0u;
 }
@@ -67,15 +100,18 @@ __device__ __forceinline__ unsigned probes(uint64_t d) {
 struct PeelParams {
     uint32_t n;
     int h;
-    const uint64_t* off;
-    const uint32_t* adj;
-    const uint64_t* split;
+    const uint64_t* off;   // row starts (read-only)
+    uint32_t* wadj;        // private copy of the rows
+    uint64_t* wend;        // row ends
+    uint64_t* wnb;         // N+ starts (h >= 3)
     unsigned long long* deg;
     uint64_t* core;
     uint32_t* rnd;
-    uint8_t* state;
+    uint32_t* sl;          // state words
     uint32_t* alive[2];
     uint32_t* front[3];
+    uint32_t* jf;          // small regime: per-slice jump candidates
+    ulonglong2* jblk;      // small regime: per-block (slice minimum, alive<<32 | candidates)
     uint2* big;
     uint64_t big_cap;
     uint64_t* lvl_k;
@@ -84,14 +120,18 @@ struct PeelParams {
     PeelCtrl* ctrl;
     uint64_t wait_ns;
     unsigned long long mu0;
-    uint32_t cap;        // per-warp candidate buffer entries (>= max |N+|, >= 32)
+    uint32_t cap;          // per-warp candidate buffer entries (>= max |N+|, >= 32)
+    int compact;           // drop removed vertices from rows as the graph shrinks
+    uint32_t work_words;   // shared words before the small-regime lists
+    uint32_t asmall;       // small-regime list capacity (0 = regime off)
 };
 
 // ------------------------------------------------------------ barrier
-__device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns) {
+__device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns, unsigned long long& waited) {
     __shared__ uint32_t s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
+        uint64_t t_in = globaltimer_ns();
         volatile uint32_t* genp = &c->bar_gen;
         uint32_t gen = *genp;
         __threadfence();
@@ -101,10 +141,9 @@ __device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns) {
             __threadfence();
             atomicAdd(&c->bar_gen, 1u);
         } else {
-            uint64_t t0 = globaltimer_ns();
             uint32_t spins = 0;
             while (*genp == gen) {
-                if (((++spins) & 255u) == 0 && globaltimer_ns() - t0 > wait_ns) {
+                if (((++spins) & 255u) == 0 && globaltimer_ns() - t_in > wait_ns) {
                     atomicOr(&c->error, kErrTimeout);
                     break;
                 }
@@ -113,6 +152,7 @@ __device__ bool grid_barrier(PeelCtrl* c, uint64_t wait_ns) {
         }
         __threadfence();
         s_err = *(volatile uint32_t*)&c->error;
+        waited += globaltimer_ns() - t_in;
     }
     __syncthreads();
     // one decision per block, so that its threads leave (or stay) together
@@ -130,11 +170,6 @@ __device__ __forceinline__ void dec_and_queue(const PeelParams& P, uint32_t u,
     }
 }
 
-__device__ __forceinline__ bool candidate(const PeelParams& P, uint32_t x, uint32_t v) {
-    uint8_t s = P.state[x];
-    return s == kAlive || (s == kFront && x > v);
-}
-
 // Warp-aggregated append of `val` where pred holds (all lanes call).
 __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t* counter,
                                             uint32_t* list) {
@@ -148,6 +183,7 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t* c
 }
 
 // Block sum of per-thread values; result valid in thread 0.
+template <int NT>
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long v,
                                                        unsigned long long* red) {
     v = warp_sum(v);
@@ -155,26 +191,51 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v,
     __syncthreads();
     unsigned long long t = 0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < kPeelWarps; w++) t += red[w];
+        for (int w = 0; w < NT / 32; w++) t += red[w];
     __syncthreads();
     return t;
 }
 
-// pre[0] = 0, pre[i+1] = sum of the degrees of F[0..i], for f <= 1024
-// entries (each thread owns 4 consecutive entries).
+// Block-wide exclusive scan of small per-thread counts; returns this
+// thread's prefix and the total in *tot (all threads).
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_count(uint32_t v, uint32_t* wtot, uint32_t* tot) {
+    unsigned lane = lane_id(), wid = warp_id();
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((int)lane >= o) x += y;
+    }
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int w = 0; w < NT / 32; w++) {
+        uint32_t t = wtot[w];
+        before += (w < (int)wid) ? t : 0u;
+        all += t;
+    }
+    __syncthreads();
+    *tot = all;
+    return before + x - v;
+}
+
+// pre[0] = 0, pre[i+1] = sum of the current row lengths of F[0..i], for
+// f <= kSmallFront entries (each thread owns kSmallFront/NT consecutive ones).
+template <int NT>
 __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const uint32_t* F,
                                                      uint32_t f, unsigned long long* pre,
                                                      unsigned long long* red) {
-    static_assert(kSmallFront == 4 * kPeelThreads, "one thread per 4 frontier entries");
-    unsigned long long d[4], sum = 0;
-    uint32_t i0 = threadIdx.x * 4;
+    constexpr int E = kSmallFront / NT;
+    unsigned long long d[E], sum = 0;
+    uint32_t i0 = threadIdx.x * E;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < E; q++) {
         uint32_t i = i0 + q;
         d[q] = 0;
         if (i < f) {
             uint32_t v = F[i];
-            d[q] = P.off[v + 1] - P.off[v];
+            d[q] = P.wend[v] - P.off[v];
         }
         sum += d[q];
     }
@@ -192,11 +253,106 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
     unsigned long long run = before + x - sum;
     if (threadIdx.x == 0) pre[0] = 0;
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < E; q++) {
         run += d[q];
         if (i0 + q < f) pre[i0 + q + 1] = run;
     }
     __syncthreads();
+}
+
+// Candidates of frontier vertex v among N+(w), in order, into C (one warp).
+// A candidate is alive, or a frontier vertex with a larger id than v, and is
+// adjacent to v: tested on v's shared bitmap `bm` (over local ids) when
+// given, else by binary search in v's row.  kChunks chunks of the row are
+// loaded at once.
+__device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint32_t v,
+                                                      uint32_t w, uint32_t* C,
+                                                      const uint32_t* bm,
+                                                      unsigned long long& bytes) {
+    unsigned lane = lane_id();
+    const uint32_t* Nv = P.wadj + P.off[v];
+    uint64_t dv = P.wend[v] - P.off[v];
+    uint64_t b = P.wnb[w], e = P.wend[w];
+    const uint64_t dw = e - b;
+    const unsigned pr = probes(dv);
+    uint32_t nc = 0;
+    // Walk the shorter side: the entries of N(v) above w, each searched in
+    // N+(w), when that costs fewer probes than walking N+(w).
+    const uint64_t cost_w = bm ? dw : dw * pr;
+    if (dv * probes(dw) < cost_w) {
+        const uint32_t* Nw = P.wadj + b;
+        uint64_t s0 = lower_bound_u32(Nv, dv, w + 1u);
+        const unsigned pw = probes(dw);
+        for (uint64_t p0 = s0; p0 < dv; p0 += 32 * kChunks) {
+            uint32_t xs[kChunks], ws[kChunks];
+#pragma unroll
+            for (int u = 0; u < kChunks; u++) {
+                uint64_t p = p0 + u * 32 + lane;
+                xs[u] = p < dv ? Nv[p] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kChunks; u++) {
+                uint64_t p = p0 + u * 32 + lane;
+                ws[u] = p < dv ? P.sl[xs[u]] : (uint32_t)kGone;
+            }
+#pragma unroll
+            for (int u = 0; u < kChunks; u++) {
+                uint64_t p = p0 + u * 32 + lane;
+                bool ok = false;
+                uint32_t x = xs[u];
+                if (p < dv) {
+                    bytes += 8;
+                    uint32_t s = st_of(ws[u]);
+                    if (s == kAlive || (s == kFront && x > v)) {
+                        uint64_t pos = lower_bound_u32(Nw, dw, x);
+                        ok = pos < dw && Nw[pos] == x;
+                        bytes += 4ull * pw;
+                    }
+                }
+                unsigned bal = __ballot_sync(0xffffffffu, ok);
+                if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
+                nc += __popc(bal);
+            }
+        }
+        return nc;
+    }
+    for (uint64_t p0 = b; p0 < e; p0 += 32 * kChunks) {
+        uint32_t xs[kChunks], ws[kChunks];
+#pragma unroll
+        for (int u = 0; u < kChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            xs[u] = p < e ? P.wadj[p] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            ws[u] = p < e ? P.sl[xs[u]] : (uint32_t)kGone;
+        }
+#pragma unroll
+        for (int u = 0; u < kChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            bool ok = false;
+            uint32_t x = xs[u];
+            if (p < e) {
+                bytes += 8;
+                uint32_t s = st_of(ws[u]);
+                if (s == kAlive || (s == kFront && x > v)) {
+                    if (bm) {
+                        uint32_t l = ws[u] >> 2;
+                        ok = (bm[l >> 5] >> (l & 31)) & 1u;
+                    } else {
+                        uint64_t pos = lower_bound_u32(Nv, dv, x);
+                        ok = pos < dv && Nv[pos] == x;
+                        bytes += 4ull * pr;
+                    }
+                }
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
+            nc += __popc(bal);
+        }
+    }
+    return nc;
 }
 
 // One (v, w) work item of a frontier vertex v with h >= 3: the cliques
@@ -204,35 +360,14 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
 // smallest such member is w.  Executed by one warp.
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
-                           uint32_t* rows, uint32_t* big_cnt, unsigned long long& destroyed,
-                           unsigned long long& bytes) {
+                           uint32_t* rows, uint32_t* big_cnt, const uint32_t* bm,
+                           unsigned long long& destroyed, unsigned long long& bytes) {
     unsigned lane = lane_id();
-    uint8_t sw = P.state[w];
-    if (lane == 0) bytes += 4 + 1;   // w, state[w]
+    uint32_t sw = st_of(P.sl[w]);
+    if (lane == 0) bytes += 4 + 4;   // w, its state word
     if (!(sw == kAlive || (sw == kFront && w > v))) return;
-    const uint32_t* Nv = P.adj + P.off[v];
-    uint64_t dv = P.off[v + 1] - P.off[v];
-    uint64_t b = P.split[w], e = P.off[w + 1];
-    if (lane == 0) bytes += 16;
-    const unsigned pr = probes(dv);
-    uint32_t nc = 0;
-    for (uint64_t p0 = b; p0 < e; p0 += 32) {
-        uint64_t p = p0 + lane;
-        bool ok = false;
-        uint32_t x = 0;
-        if (p < e) {
-            x = P.adj[p];
-            bytes += 4 + 1;
-            if (candidate(P, x, v)) {
-                uint64_t pos = lower_bound_u32(Nv, dv, x);
-                ok = pos < dv && Nv[pos] == x;
-                bytes += 4ull * pr;
-            }
-        }
-        unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
-        nc += __popc(bal);
-    }
+    if (lane == 0) bytes += 16;      // wnb[w], wend[w]
+    uint32_t nc = gather_candidates(P, v, w, C, bm, bytes);
     __syncwarp();
     const int r = P.h - 2;
     unsigned long long tot = 0;
@@ -240,8 +375,8 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         tot = nc;
         for (uint32_t i = lane; i < nc; i += 32) {
             uint32_t x = C[i];
-            bytes += 1;
-            if (P.state[x] == kAlive) {
+            bytes += 4;
+            if (st_of(P.sl[x]) == kAlive) {
                 dec_and_queue(P, x, 1ull, k, next, next_cnt);
                 bytes += 16;
             }
@@ -262,11 +397,11 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
             // edges of G[C]: each is a clique {v, w, x, y}
             for (uint32_t i = 0; i < nc; i++) {
                 uint32_t x = C[i];
-                uint64_t xb = P.split[x], xe = P.off[x + 1];
+                uint64_t xb = P.wnb[x], xe = P.wend[x];
                 unsigned hits = 0;
                 if (lane == 0) bytes += 16;
                 for (uint64_t p = xb + lane; p < xe; p += 32) {
-                    uint32_t y = P.adj[p];
+                    uint32_t y = P.wadj[p];
                     bytes += 4;
                     uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
                     if (pos < nc && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
@@ -278,8 +413,8 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         } else {
             if (lane == 0)
                 for (uint32_t i = 0; i < nc; i++)
-                    bytes += 16 + 4ull * (P.off[C[i] + 1] - P.split[C[i]]);
-            warp_build_rows32(C, nc, P.off, P.adj, P.split, rows);
+                    bytes += 16 + 4ull * (P.wend[C[i]] - P.wnb[C[i]]);
+            warp_build_rows32(C, nc, P.wend, P.wadj, P.wnb, rows);
             tot = warp_dfs32(rows, nc, r, cnt);
         }
         __syncwarp();
@@ -287,8 +422,8 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
             for (uint32_t i = lane; i < nc; i += 32) {
                 uint32_t x = C[i];
                 if (cnt[i]) {
-                    bytes += 1;
-                    if (P.state[x] == kAlive) {
+                    bytes += 4;
+                    if (st_of(P.sl[x]) == kAlive) {
                         dec_and_queue(P, x, (unsigned long long)cnt[i], k, next, next_cnt);
                         bytes += 16;
                     }
@@ -308,43 +443,31 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
 // A (v, w) item whose candidate set exceeds 32 vertices (h >= 5): one block.
 __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                             uint32_t* next, uint32_t* next_cnt, uint32_t* smem,
-                            unsigned long long& destroyed) {
+                            unsigned long long& destroyed, unsigned long long& bytes) {
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // cap
     uint32_t* C = smem + 2 * P.cap;                                           // cap
     uint32_t* rows = C + P.cap;                                               // cap * W
     __shared__ uint32_t s_nc;
     __shared__ unsigned long long s_tot;
-    unsigned lane = lane_id();
-    uint8_t sw = P.state[w];
+    uint32_t sw = st_of(P.sl[w]);
     if (warp_id() == 0) {
-        const uint32_t* Nv = P.adj + P.off[v];
-        uint64_t dv = P.off[v + 1] - P.off[v];
-        uint64_t b = P.split[w], e = P.off[w + 1];
-        uint32_t nc = 0;
-        for (uint64_t p0 = b; p0 < e; p0 += 32) {
-            uint64_t p = p0 + lane;
-            bool ok = false;
-            uint32_t x = 0;
-            if (p < e) {
-                x = P.adj[p];
-                if (candidate(P, x, v)) {
-                    uint64_t pos = lower_bound_u32(Nv, dv, x);
-                    ok = pos < dv && Nv[pos] == x;
-                }
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, ok);
-            if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
-            nc += __popc(bal);
+        uint32_t nc = gather_candidates(P, v, w, C, nullptr, bytes);
+        if (lane_id() == 0) {
+            s_nc = nc;
+            s_tot = 0;
+            bytes += 4 + 4 + 16;
         }
-        if (lane == 0) { s_nc = nc; s_tot = 0; }
     }
     __syncthreads();
     uint32_t nc = s_nc;
     uint32_t W = (nc + 31) >> 5;
-    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) cnt[i] = 0;
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+        cnt[i] = 0;
+        bytes += 16 + 4ull * (P.wend[C[i]] - P.wnb[C[i]]);
+    }
     for (uint32_t i = threadIdx.x; i < nc * W; i += blockDim.x) rows[i] = 0;
     __syncthreads();
-    block_build_rows(C, nc, W, P.off, P.adj, P.split, rows);
+    block_build_rows(C, nc, W, P.wend, P.wadj, P.wnb, rows);
     __syncthreads();
     unsigned long long mine = block_dfs(rows, nc, W, P.h - 2, cnt);
     if (mine) atomicAdd(&s_tot, mine);
@@ -353,7 +476,10 @@ __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigne
     if (tot) {
         for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
             uint32_t x = C[i];
-            if (cnt[i] && P.state[x] == kAlive) dec_and_queue(P, x, cnt[i], k, next, next_cnt);
+            if (cnt[i] && st_of(P.sl[x]) == kAlive) {
+                dec_and_queue(P, x, cnt[i], k, next, next_cnt);
+                bytes += 20;
+            }
         }
         if (threadIdx.x == 0) {
             if (sw == kAlive) dec_and_queue(P, w, tot, k, next, next_cnt);
@@ -363,11 +489,165 @@ __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigne
     __syncthreads();
 }
 
+// Drop removed vertices from row v in place (one warp); rows stay sorted.
+__device__ __forceinline__ void compact_row(const PeelParams& P, uint32_t v,
+                                            unsigned long long& bytes) {
+    unsigned lane = lane_id();
+    uint64_t b = P.off[v], e = P.wend[v];
+    uint64_t outp = b;
+    uint64_t below = 0;   // kept entries smaller than v
+    for (uint64_t p0 = b; p0 < e; p0 += 32) {
+        uint64_t p = p0 + lane;
+        uint32_t x = 0;
+        bool keep = false;
+        if (p < e) {
+            x = P.wadj[p];
+            keep = st_of(P.sl[x]) != kGone;
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        unsigned lt = __ballot_sync(0xffffffffu, keep && x < v);
+        // every lane has read its entry before any lane writes
+        if (keep) P.wadj[outp + __popc(bal & ((1u << lane) - 1u))] = x;
+        outp += __popc(bal);
+        below += __popc(lt);
+        __syncwarp();
+    }
+    bytes += 8ull * (e - b) + 4ull * (outp - b);
+    if (lane == 0) {
+        P.wend[v] = outp;
+        P.wnb[v] = b + below;
+        bytes += 16;
+    }
+}
+
+// P2: the cliques destroyed by frontier F (nf vertices; F in global or
+// shared memory, identical for every block).  bm: shared bitmaps of the
+// neighbourhoods of F[0 .. min(nf, kBitmapSlots)) (small regime), or null.
+template <int NT>
+__device__ __forceinline__ void process_frontier(
+    const PeelParams& P, const uint32_t* F, uint32_t nf, unsigned long long k, uint32_t* Fnext,
+    uint32_t* next_cnt, uint32_t* big_cnt, uint32_t* wC, unsigned* wCnt, uint32_t* wRows,
+    const uint32_t* bm, uint32_t bm_words, unsigned long long* s_pre, unsigned long long* s_red,
+    unsigned long long& destroyed, unsigned long long& items, unsigned long long& bytes) {
+    constexpr int NW = NT / 32;
+    const unsigned lane = lane_id(), wid = warp_id();
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gwarp = gtid >> 5;
+    const uint64_t gwarps = gthreads >> 5;
+    if (nf <= kSmallFront) {
+        // flatten (v, neighbour index) items over the whole grid
+        block_prefix_degrees<NT>(P, F, nf, s_pre, s_red);
+        unsigned long long T = s_pre[nf];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            items += T;
+            bytes += 20ull * nf;   // frontier ids and their row bounds
+        }
+        if (P.h == 2) {
+            for (uint64_t t = gtid; t < T; t += gthreads) {
+                uint32_t lo = 0, hi = nf;  // last i with s_pre[i] <= t
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (s_pre[mid] <= t) lo = mid; else hi = mid;
+                }
+                uint32_t v = F[lo];
+                uint32_t u = P.wadj[P.off[v] + (t - s_pre[lo])];
+                uint32_t su = st_of(P.sl[u]);
+                bytes += 4 + 4;
+                if (su == kAlive) {
+                    dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
+                    destroyed++;
+                    bytes += 16;
+                } else if (su == kFront && u > v) {
+                    destroyed++;
+                }
+            }
+        } else {
+            for (uint64_t t = gwarp; t < T; t += gwarps) {
+                uint32_t lo = 0, hi = nf;
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (s_pre[mid] <= t) lo = mid; else hi = mid;
+                }
+                uint32_t v = F[lo];
+                uint32_t w = P.wadj[P.off[v] + (t - s_pre[lo])];
+                const uint32_t* vbm = (bm && lo < kBitmapSlots) ? bm + (size_t)lo * bm_words : nullptr;
+                process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, vbm, destroyed,
+                           bytes);
+            }
+        }
+    } else if (P.h == 2) {
+        for (uint64_t i = gwarp; i < nf; i += gwarps) {
+            uint32_t v = F[i];
+            uint64_t b = P.off[v], e = P.wend[v];
+            for (uint64_t p = b + lane; p < e; p += 32) {
+                uint32_t u = P.wadj[p];
+                uint32_t su = st_of(P.sl[u]);
+                bytes += 4 + 4;
+                if (su == kAlive) {
+                    dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
+                    destroyed++;
+                    bytes += 16;
+                } else if (su == kFront && u > v) {
+                    destroyed++;
+                }
+            }
+            if (lane == 0) {
+                items += e - b;
+                bytes += 20;
+            }
+        }
+    } else {
+        for (uint64_t i = blockIdx.x; i < nf; i += gridDim.x) {
+            uint32_t v = F[i];
+            uint64_t b = P.off[v], e = P.wend[v];
+            const uint32_t* vbm = (bm && i < kBitmapSlots) ? bm + (size_t)i * bm_words : nullptr;
+            for (uint64_t p = b + wid; p < e; p += NW)
+                process_vw(P, v, P.wadj[p], k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, vbm,
+                           destroyed, bytes);
+            if (threadIdx.x == 0) {
+                items += e - b;
+                bytes += 20;
+            }
+        }
+    }
+}
+
+// Shared bitmaps over local ids of the neighbourhoods of F[0..min(nf,
+// kBitmapSlots)), built by every block (small regime).
+template <int NT>
+__device__ __forceinline__ void build_bitmaps(const PeelParams& P, const uint32_t* F, uint32_t nf,
+                                              uint32_t* bm, uint32_t bm_words) {
+    uint32_t slots = nf < kBitmapSlots ? nf : kBitmapSlots;
+    for (uint32_t i = threadIdx.x; i < slots * bm_words; i += NT) bm[i] = 0;
+    __syncthreads();
+    const unsigned nw = NT / 32;
+    for (uint32_t s = warp_id(); s < slots; s += nw) {
+        uint32_t v = F[s];
+        uint64_t b = P.off[v], e = P.wend[v];
+        uint32_t* row = bm + (size_t)s * bm_words;
+        for (uint64_t p = b + lane_id(); p < e; p += 32) {
+            uint32_t x = P.wadj[p];
+            uint32_t w = P.sl[x];
+            // removed vertices may lack a local id; they are never candidates
+            if (st_of(w) != kGone) {
+                uint32_t l = w >> 2;
+                atomicOr(&row[l >> 5], 1u << (l & 31));
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
+    constexpr int NW = NT / 32;
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_pre[kSmallFront + 1];
-    __shared__ unsigned long long s_red[kPeelWarps];
+    __shared__ unsigned long long s_red[NW];
+    __shared__ uint32_t s_wtot[NW];
+    __shared__ uint32_t s_n;
     PeelCtrl* c = P.ctrl;
     const unsigned lane = lane_id(), wid = warp_id();
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,204 +657,393 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
     uint32_t* wC = smem + (size_t)wid * (2 * P.cap + 32);
     unsigned* wCnt = wC + P.cap;
     uint32_t* wRows = wC + 2 * P.cap;
+    uint32_t* sA = smem + P.work_words;   // small regime: alive list
+    uint32_t* sF = sA + P.asmall;         // small regime: frontier
+    uint32_t* sBM = sF + P.asmall;        // small regime: neighbourhood bitmaps
+    const uint32_t bm_words = (P.asmall + 31) / 32;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
 
     unsigned long long k = 0;
     unsigned long long mu_alive = P.mu0;   // meaningful in block 0
-    uint32_t r = 0, jumps = 0, nlev = 0;
+    uint32_t r = 0, jumps = 0, nlev = 0, nbar = 0, ncompact = 0;
     int ap = 0;
     uint32_t alive_cnt = P.n;
-    unsigned long long items = 0;
-    unsigned long long bytes = 0;
+    uint32_t compacted_at = P.n;           // alive count at the last row compaction
+    bool small = false;
+    uint32_t na_s = 0, nf_s = 0;           // small regime: alive total, frontier size
+    uint32_t na_entry = 0;                 // alive vertices when the small regime began
+    uint32_t slice_lo = 0, na_loc = 0;     // this block's slice of the alive list
+    uint32_t cmp_loc = 0;                  // slice size at its last row compaction
+    unsigned long long items = 0, bytes = 0, waited = 0;
+
+    // Block 0's time per phase (thread 0, %globaltimer); the time inside
+    // barriers is counted separately in `waited`.
+    __shared__ unsigned long long tph[8];
+    if (threadIdx.x < 8) tph[threadIdx.x] = 0;
+    uint64_t tlast = lead ? globaltimer_ns() : 0;
+#define PHASE(i)                                 \
+    do {                                         \
+        if (lead) {                              \
+            uint64_t t_ = globaltimer_ns();      \
+            tph[i] += t_ - tlast;                \
+            tlast = t_;                          \
+        }                                        \
+    } while (0)
+#define BARRIER(i)                                         \
+    do {                                                   \
+        PHASE(i);                                          \
+        nbar++;                                            \
+        if (!grid_barrier(c, P.wait_ns, waited)) goto out; \
+        if (lead) tlast = globaltimer_ns();                \
+    } while (0)
 
     for (;;) {
-        // ---------------------------------------------------------- P1
-        uint32_t fprev = r ? c->fcnt[(r + 2) % 3] : 0u;
-        const uint32_t* Fprev = P.front[(r + 2) % 3];
-        for (uint64_t i = gtid; i < fprev; i += gthreads) {
-            uint32_t v = Fprev[i];
-            P.state[v] = kGone;
-            P.core[v] = k;
-            if (P.rnd) P.rnd[v] = r - 1;
-            bytes += 4 + 1 + 8 + (P.rnd ? 4 : 0);
+        bool s_jump = false;
+        if (!small) {
+            // ------------------------------------------------------ P1
+            {
+                uint32_t fprev = r ? c->fcnt[(r + 2) % 3] : 0u;
+                const uint32_t* Fprev = P.front[(r + 2) % 3];
+                for (uint64_t i = gtid; i < fprev; i += gthreads) {
+                    uint32_t v = Fprev[i];
+                    P.sl[v] = kGone;
+                    P.core[v] = k;
+                    if (P.rnd) P.rnd[v] = r - 1;
+                    bytes += 4 + 4 + 8 + (P.rnd ? 4 : 0);
+                }
+            }
+            uint32_t fcur = c->fcnt[r % 3];
+            uint32_t* Fcur = P.front[r % 3];
+            for (uint64_t i = gtid; i < fcur; i += gthreads) {
+                P.sl[Fcur[i]] = kFront;
+                bytes += 4 + 4;
+            }
+            if (lead) {
+                if (r) {
+                    mu_alive -= c->destroyed[(r + 2) % 3];
+                    c->destroyed[(r + 2) % 3] = 0;
+                    c->big_cnt[(r + 2) % 3] = 0;
+                }
+                c->fcnt[(r + 1) % 3] = 0;
+            }
+            BARRIER(0);
+
+            // ------------------------------------------------- level jump
+            if (fcur == 0) {
+                const uint32_t* Ain = P.alive[ap];
+                uint32_t* Aout = P.alive[ap ^ 1];
+                unsigned long long mn = ~0ull;
+                for (uint64_t base = gwarp * 32; base < alive_cnt; base += gwarps * 32) {
+                    uint64_t i = base + lane;
+                    bool keep = false;
+                    uint32_t v = 0;
+                    if (i < alive_cnt) {
+                        v = Ain[i];
+                        bytes += 4 + 4;
+                        if (st_of(P.sl[v]) != kGone) {
+                            keep = true;
+                            unsigned long long d = P.deg[v];
+                            mn = d < mn ? d : mn;
+                            bytes += 8 + 4;
+                        }
+                    }
+                    warp_append(keep, v, &c->new_alive[jumps & 1], Aout);
+                }
+                mn = warp_min_u64(mn);
+                if (lane == 0 && mn != ~0ull) atomicMin(&c->min_deg[jumps & 1], mn);
+                BARRIER(1);
+                uint32_t na = c->new_alive[jumps & 1];
+                if (na == 0) break;
+                ap ^= 1;
+                alive_cnt = na;
+                if (na <= P.asmall) {
+                    // enter the small regime: each block keeps its slice of
+                    // the alive list in shared memory and gives those vertices
+                    // their local id (the position in the list)
+                    na_entry = na;
+                    slice_lo = (uint32_t)((uint64_t)na * blockIdx.x / gridDim.x);
+                    na_loc = (uint32_t)((uint64_t)na * (blockIdx.x + 1) / gridDim.x) - slice_lo;
+                    cmp_loc = na_loc;
+                    for (uint32_t i = threadIdx.x; i < na_loc; i += NT) {
+                        uint32_t v = Aout[slice_lo + i];
+                        sA[i] = v;
+                        P.sl[v] = ((slice_lo + i) << 2) | kAlive;
+                    }
+                    if (lead) {
+                        c->small_round = r;
+                        bytes += 12ull * na;
+                    }
+                    small = true;
+                    na_s = na;
+                    nf_s = 0;
+                    s_jump = true;
+                    __syncthreads();
+                } else {
+                    unsigned long long m2 = c->min_deg[jumps & 1];
+                    k = m2 > k ? m2 : k;
+                    if (lead) {
+                        P.lvl_k[nlev] = k;
+                        P.lvl_size[nlev] = na;
+                        P.lvl_mu[nlev] = mu_alive;
+                        c->min_deg[(jumps + 1) & 1] = ~0ull;
+                        c->new_alive[(jumps + 1) & 1] = 0;
+                    }
+                    nlev++;
+                    jumps++;
+                    // Rows may be compacted in this same phase: compaction keeps
+                    // every vertex that is not removed, whether or not it is
+                    // being marked frontier concurrently.
+                    if (P.compact && 2ull * na <= compacted_at) {
+                        compacted_at = na;
+                        ncompact++;
+                        for (uint64_t i = gwarp; i < na; i += gwarps) compact_row(P, Aout[i], bytes);
+                    }
+                    for (uint64_t base = gwarp * 32; base < na; base += gwarps * 32) {
+                        uint64_t i = base + lane;
+                        bool in = false;
+                        uint32_t v = 0;
+                        if (i < na) {
+                            v = Aout[i];
+                            bytes += 4 + 8;
+                            if (P.deg[v] <= k) {
+                                in = true;
+                                P.sl[v] = kFront;
+                                bytes += 4 + 4;
+                            }
+                        }
+                        warp_append(in, v, &c->fcnt[r % 3], Fcur);
+                    }
+                    BARRIER(2);
+                    fcur = c->fcnt[r % 3];
+                }
+            }
+            if (!small) {
+                // -------------------------------------------------- P2
+                unsigned long long destroyed = 0;
+                process_frontier<NT>(P, Fcur, fcur, k, P.front[(r + 1) % 3],
+                                     &c->fcnt[(r + 1) % 3], &c->big_cnt[r % 3], wC, wCnt,
+                                     wRows, nullptr, 0, s_pre, s_red, destroyed, items, bytes);
+                unsigned long long bd = block_sum<NT>(destroyed, s_red);
+                if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
+                BARRIER(3);
+                // ------------------------------------------------- P2b
+                if (P.h >= 5) {
+                    uint32_t nb = c->big_cnt[r % 3];
+                    if (nb) {
+                        if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
+                        unsigned long long d2 = 0;
+                        for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+                            uint2 it = P.big[i];
+                            process_big(P, it.x, it.y, k, P.front[(r + 1) % 3],
+                                        &c->fcnt[(r + 1) % 3], smem, d2, bytes);
+                        }
+                        if (threadIdx.x == 0 && d2) atomicAdd(&c->destroyed[r % 3], d2);
+                        BARRIER(3);
+                    }
+                }
+                r++;
+                continue;
+            }
         }
-        uint32_t fcur = c->fcnt[r % 3];
-        uint32_t* Fcur = P.front[r % 3];
-        for (uint64_t i = gtid; i < fcur; i += gthreads) {
-            P.state[Fcur[i]] = kFront;
-            bytes += 4 + 1;
-        }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            if (r) {
+
+        // ========================================================= small
+        if (!s_jump) {
+            // retire F_{r-1}: identical writes in every block
+            for (uint32_t i = threadIdx.x; i < nf_s; i += NT) {
+                uint32_t v = sF[i];
+                P.sl[v] = (P.sl[v] & ~3u) | kGone;
+                P.core[v] = k;
+                if (P.rnd) P.rnd[v] = r - 1;
+            }
+            if (lead) bytes += (20ull + (P.rnd ? 4 : 0)) * nf_s;
+            if (lead) {
                 mu_alive -= c->destroyed[(r + 2) % 3];
                 c->destroyed[(r + 2) % 3] = 0;
                 c->big_cnt[(r + 2) % 3] = 0;
             }
-            c->fcnt[(r + 1) % 3] = 0;
-        }
-        if (!grid_barrier(c, P.wait_ns)) break;
-
-        // ----------------------------------------------------- level jump
-        if (fcur == 0) {
-            const uint32_t* Ain = P.alive[ap];
-            uint32_t* Aout = P.alive[ap ^ 1];
-            unsigned long long mn = ~0ull;
-            for (uint64_t base = gwarp * 32; base < alive_cnt; base += gwarps * 32) {
-                uint64_t i = base + lane;
-                bool keep = false;
-                uint32_t v = 0;
-                if (i < alive_cnt) {
-                    v = Ain[i];
-                    bytes += 4 + 1;
-                    if (P.state[v] != kGone) {
-                        keep = true;
-                        unsigned long long d = P.deg[v];
-                        mn = d < mn ? d : mn;
-                        bytes += 8 + 4;
-                    }
-                }
-                warp_append(keep, v, &c->new_alive[jumps & 1], Aout);
+            uint32_t nf_new = c->fcnt[r % 3];
+            __syncthreads();
+            if (nf_new) {
+                const uint32_t* G = P.front[r % 3];
+                for (uint32_t i = threadIdx.x; i < nf_new; i += NT) sF[i] = G[i];
+                if (lead) bytes += 4ull * nf_new;
+                nf_s = nf_new;
+            } else {
+                s_jump = true;
             }
-            mn = warp_min_u64(mn);
-            if (lane == 0 && mn != ~0ull) atomicMin(&c->min_deg[jumps & 1], mn);
-            if (!grid_barrier(c, P.wait_ns)) break;
-            uint32_t na = c->new_alive[jumps & 1];
-            if (na == 0) break;
-            unsigned long long m2 = c->min_deg[jumps & 1];
-            k = m2 > k ? m2 : k;
-            ap ^= 1;
-            alive_cnt = na;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                P.lvl_k[nlev] = k;
-                P.lvl_size[nlev] = na;
-                P.lvl_mu[nlev] = mu_alive;
+        }
+        // the counter that collects round r+2's appends was last read at the
+        // start of round r-1
+        if (lead) c->fcnt[(r + 2) % 3] = 0;
+        PHASE(4);
+        if (s_jump) {
+            // Level jump over the alive set, distributed: each block compacts
+            // its own slice (kept in shared memory), takes the slice minimum
+            // and the slice vertices attaining it, and publishes them; after
+            // the barrier every block combines the slice minima and gathers the
+            // frontier from the slices that attain the global minimum.
+            uint32_t kept = 0;
+            unsigned long long lmin = ~0ull;
+            {
+                if (threadIdx.x == 0) s_n = 0;
+                __syncthreads();
+                for (uint32_t base = 0; base < na_loc; base += NT) {
+                    uint32_t i = base + threadIdx.x;
+                    uint32_t v = i < na_loc ? sA[i] : 0u;
+                    uint32_t s = i < na_loc ? st_of(P.sl[v]) : (uint32_t)kGone;
+                    unsigned long long d = i < na_loc ? P.deg[v] : ~0ull;
+                    bool keep = s == kAlive;
+                    if (keep) lmin = d < lmin ? d : lmin;
+                    uint32_t tot;
+                    uint32_t at = block_scan_count<NT>(keep ? 1u : 0u, s_wtot, &tot);
+                    uint32_t o = s_n;
+                    __syncthreads();   // every read of this pass precedes any write
+                    if (keep) sA[o + at] = v;
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_n = o + tot;
+                }
+                __syncthreads();
+                kept = s_n;
+                if (lead) bytes += 16ull * na_entry;
+            }
+            lmin = warp_min_u64(lmin);
+            if (lane == 0) s_red[wid] = lmin;
+            __syncthreads();
+            lmin = ~0ull;
+            for (int w = 0; w < NW; w++) lmin = s_red[w] < lmin ? s_red[w] : lmin;
+            __syncthreads();
+            na_loc = kept;
+            // the slice vertices attaining the slice minimum, published in
+            // this block's part of the jump list
+            {
+                if (threadIdx.x == 0) s_n = 0;
+                __syncthreads();
+                for (uint32_t base = 0; base < na_loc; base += NT) {
+                    uint32_t i = base + threadIdx.x;
+                    uint32_t v = i < na_loc ? sA[i] : 0u;
+                    bool in = i < na_loc && P.deg[v] == lmin;
+                    uint32_t tot;
+                    uint32_t at = block_scan_count<NT>(in ? 1u : 0u, s_wtot, &tot);
+                    uint32_t o = s_n;
+                    if (in) P.jf[slice_lo + o + at] = v;
+                    __syncthreads();
+                    if (threadIdx.x == 0) s_n = o + tot;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    P.jblk[blockIdx.x] = make_ulonglong2(lmin, ((unsigned long long)na_loc << 32) | s_n);
+                }
+            }
+            // rows of this slice lose their removed entries once the slice
+            // has halved (no block reads rows during this phase)
+            if (P.compact && 2ull * na_loc <= cmp_loc) {
+                cmp_loc = na_loc;
+                ncompact++;
+                for (uint32_t i = wid; i < na_loc; i += NW) compact_row(P, sA[i], bytes);
+            }
+            // Every block must have read the counts for this jump before any
+            // block starts the round's decrements.
+            BARRIER(5);
+            // combine: global minimum, alive count, and the frontier
+            {
+                unsigned long long gm = ~0ull;
+                unsigned long long tot_alive = 0;
+                uint32_t cnt_t = 0;
+                unsigned long long min_t = ~0ull;
+                if (threadIdx.x < gridDim.x) {
+                    ulonglong2 e = P.jblk[threadIdx.x];
+                    min_t = e.x;
+                    tot_alive = e.y >> 32;
+                    cnt_t = (uint32_t)(e.y & 0xffffffffull);
+                    gm = min_t;
+                }
+                gm = warp_min_u64(gm);
+                tot_alive = warp_sum(tot_alive);
+                if (lane == 0) {
+                    s_red[wid] = gm;
+                    s_pre[wid] = tot_alive;
+                }
+                __syncthreads();
+                gm = ~0ull;
+                tot_alive = 0;
+                for (int w = 0; w < NW; w++) {
+                    gm = s_red[w] < gm ? s_red[w] : gm;
+                    tot_alive += s_pre[w];
+                }
+                __syncthreads();
+                if (tot_alive == 0) break;
+                k = gm > k ? gm : k;
+                na_s = (uint32_t)tot_alive;
+                if (lead) {
+                    P.lvl_k[nlev] = k;
+                    P.lvl_size[nlev] = na_s;
+                    P.lvl_mu[nlev] = mu_alive;
+                }
                 nlev++;
-                c->min_deg[(jumps + 1) & 1] = ~0ull;
-                c->new_alive[(jumps + 1) & 1] = 0;
-            }
-            jumps++;
-            for (uint64_t base = gwarp * 32; base < na; base += gwarps * 32) {
-                uint64_t i = base + lane;
-                bool in = false;
-                uint32_t v = 0;
-                if (i < na) {
-                    v = Aout[i];
-                    bytes += 4 + 8;
-                    if (P.deg[v] <= k) {
-                        in = true;
-                        P.state[v] = kFront;
-                        bytes += 1 + 4;
-                    }
+                // frontier = the published vertices of slices whose minimum is gm
+                uint32_t take = (threadIdx.x < gridDim.x && min_t == gm) ? cnt_t : 0u;
+                uint32_t tot;
+                uint32_t at = block_scan_count<NT>(take, s_wtot, &tot);
+                if (threadIdx.x < gridDim.x) {
+                    s_pre[threadIdx.x] = ((unsigned long long)at << 32) | take;
                 }
-                warp_append(in, v, &c->fcnt[r % 3], Fcur);
-            }
-            if (!grid_barrier(c, P.wait_ns)) break;
-            fcur = c->fcnt[r % 3];
-        }
-
-        // ----------------------------------------------------------- P2
-        uint32_t* Fnext = P.front[(r + 1) % 3];
-        uint32_t* next_cnt = &c->fcnt[(r + 1) % 3];
-        unsigned long long destroyed = 0;
-        if (fcur <= kSmallFront) {
-            // flatten (v, neighbour index) items over the whole grid
-            block_prefix_degrees(P, Fcur, fcur, s_pre, s_red);
-            unsigned long long T = s_pre[fcur];
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                items += T;
-                bytes += 20ull * fcur;   // frontier ids and their offsets
-            }
-            if (P.h == 2) {
-                for (uint64_t t = gtid; t < T; t += gthreads) {
-                    uint32_t lo = 0, hi = fcur;  // last i with s_pre[i] <= t
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (s_pre[mid] <= t) lo = mid; else hi = mid;
-                    }
-                    uint32_t v = Fcur[lo];
-                    uint32_t u = P.adj[P.off[v] + (t - s_pre[lo])];
-                    uint8_t su = P.state[u];
-                    bytes += 4 + 1;
-                    if (su == kAlive) {
-                        dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
-                        destroyed++;
-                        bytes += 16;
-                    } else if (su == kFront && u > v) {
-                        destroyed++;
-                    }
+                __syncthreads();
+                for (uint32_t t = wid; t < gridDim.x; t += NW) {
+                    unsigned long long e = s_pre[t];
+                    uint32_t ct = (uint32_t)(e & 0xffffffffull), o = (uint32_t)(e >> 32);
+                    uint64_t lo = (uint64_t)na_entry * t / gridDim.x;
+                    for (uint32_t j = lane; j < ct; j += 32) sF[o + j] = P.jf[lo + j];
                 }
-            } else {
-                for (uint64_t t = gwarp; t < T; t += gwarps) {
-                    uint32_t lo = 0, hi = fcur;
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (s_pre[mid] <= t) lo = mid; else hi = mid;
-                    }
-                    uint32_t v = Fcur[lo];
-                    uint32_t w = P.adj[P.off[v] + (t - s_pre[lo])];
-                    process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows,
-                               &c->big_cnt[r % 3], destroyed, bytes);
-                }
-            }
-        } else {
-            if (P.h == 2) {
-                for (uint64_t i = gwarp; i < fcur; i += gwarps) {
-                    uint32_t v = Fcur[i];
-                    uint64_t b = P.off[v], e = P.off[v + 1];
-                    for (uint64_t p = b + lane; p < e; p += 32) {
-                        uint32_t u = P.adj[p];
-                        uint8_t su = P.state[u];
-                        bytes += 4 + 1;
-                        if (su == kAlive) {
-                            dec_and_queue(P, u, 1ull, k, Fnext, next_cnt);
-                            destroyed++;
-                            bytes += 16;
-                        } else if (su == kFront && u > v) {
-                            destroyed++;
-                        }
-                    }
-                    if (lane == 0) {
-                        items += e - b;
-                        bytes += 20;
-                    }
-                }
-            } else {
-                for (uint64_t i = blockIdx.x; i < fcur; i += gridDim.x) {
-                    uint32_t v = Fcur[i];
-                    uint64_t b = P.off[v], e = P.off[v + 1];
-                    for (uint64_t p = b + wid; p < e; p += kPeelWarps)
-                        process_vw(P, v, P.adj[p], k, Fnext, next_cnt, wC, wCnt, wRows,
-                                   &c->big_cnt[r % 3], destroyed, bytes);
-                    if (threadIdx.x == 0) {
-                        items += e - b;
-                        bytes += 20;
-                    }
-                }
+                nf_s = tot;
+                if (lead) bytes += 16ull * gridDim.x + 8ull * nf_s;
+                __syncthreads();
             }
         }
-        unsigned long long bd = block_sum(destroyed, s_red);
-        if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
-        if (!grid_barrier(c, P.wait_ns)) break;
-
-        // ---------------------------------------------------------- P2b
-        if (P.h >= 5) {
-            uint32_t nb = c->big_cnt[r % 3];
-            if (nb) {
-                if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
-                unsigned long long d2 = 0;
-                for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
-                    uint2 it = P.big[i];
-                    process_big(P, it.x, it.y, k, Fnext, next_cnt, smem, d2);
+        // mark the frontier (identical writes in every block)
+        for (uint32_t i = threadIdx.x; i < nf_s; i += NT) {
+            uint32_t v = sF[i];
+            P.sl[v] = (P.sl[v] & ~3u) | kFront;
+        }
+        if (lead) bytes += 8ull * nf_s;
+        __syncthreads();
+        if (P.h >= 3) build_bitmaps<NT>(P, sF, nf_s, sBM, bm_words);
+        PHASE(6);
+        {
+            unsigned long long destroyed = 0;
+            process_frontier<NT>(P, sF, nf_s, k, P.front[(r + 1) % 3], &c->fcnt[(r + 1) % 3],
+                                 &c->big_cnt[r % 3], wC, wCnt, wRows, P.h >= 3 ? sBM : nullptr,
+                                 bm_words, s_pre, s_red, destroyed, items, bytes);
+            unsigned long long bd = block_sum<NT>(destroyed, s_red);
+            if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
+            BARRIER(7);
+            if (P.h >= 5) {
+                uint32_t nb = c->big_cnt[r % 3];
+                if (nb) {
+                    if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
+                    unsigned long long d2 = 0;
+                    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+                        uint2 it = P.big[i];
+                        process_big(P, it.x, it.y, k, P.front[(r + 1) % 3],
+                                    &c->fcnt[(r + 1) % 3], smem, d2, bytes);
+                    }
+                    if (threadIdx.x == 0 && d2) atomicAdd(&c->destroyed[r % 3], d2);
+                    BARRIER(7);
                 }
-                if (threadIdx.x == 0 && d2) atomicAdd(&c->destroyed[r % 3], d2);
-                if (!grid_barrier(c, P.wait_ns)) break;
             }
         }
         r++;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+out:
+#undef BARRIER
+#undef PHASE
+    if (lead) {
+        for (int i = 0; i < 8; i++) c->tph[i] = tph[i];
         c->kmax = k;
         c->nlevels = nlev;
         c->rounds = r;
+        c->barrier_ns = waited;
+        c->barriers = nbar;
+        c->compactions = ncompact;
     }
     items = warp_sum(items);
     bytes = warp_sum(bytes);
@@ -582,16 +1051,41 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(PeelParams P) {
     if (lane == 0 && bytes) atomicAdd(&c->bytes, bytes);
 }
 
-__global__ void k_peel_init(uint32_t n, uint8_t* state, uint32_t* alive0, PeelCtrl* c) {
+__global__ void k_peel_init(uint32_t n, const uint64_t* off, const uint64_t* split,
+                            uint32_t* sl, uint32_t* alive0, uint64_t* wend, uint64_t* wnb,
+                            PeelCtrl* c) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        state[i] = kAlive;
+        sl[i] = kAlive;
         alive0[i] = (uint32_t)i;
+        wend[i] = off[i + 1];
+        wnb[i] = split ? split[i] : off[i];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->min_deg[0] = ~0ull;
         c->min_deg[1] = ~0ull;
     }
+}
+
+template <int NT>
+cudaError_t launch_peel(PeelParams& P, int sms, size_t smem, cudaStream_t s, unsigned* grid_out) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024)
+        e = cudaFuncSetAttribute(k_peel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel<NT>, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    // one block per SM: the fewest barrier arrivals; every block holds the
+    // small-regime lists in its own shared memory
+    unsigned grid = (unsigned)sms;
+    *grid_out = grid;
+    void* args[] = {&P};
+    e = cudaLaunchCooperativeKernel((void*)k_peel<NT>, dim3(grid), dim3(NT), args, smem, s);
+    note_launch();
+    return e;
 }
 
 }  // namespace
@@ -610,8 +1104,6 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.n = n;
     P.h = h;
     P.off = off;
-    P.adj = adj;
-    P.split = split;
     P.deg = deg;
     P.core = core;
     P.rnd = rnd;
@@ -621,62 +1113,89 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.wait_ns = wait_limit_ns();
     P.mu0 = mu0;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
-    size_t warp_words = (size_t)2 * P.cap + 32;
-    size_t smem = h >= 3 ? warp_words * kPeelWarps * 4 : 0;
-    if (h >= 5) {
-        uint32_t W = (P.cap + 31) / 32;
-        size_t big = ((size_t)3 * P.cap + (size_t)P.cap * W) * 4;
-        if (big > smem) smem = big;
-        if (maxdplus > kBitmapMax) {
-            set_error("h=%d peeling needs at most %u higher-ranked neighbours per vertex "
-                      "(max here %u)", h, kBitmapMax, maxdplus);
-            return DSD_ERR_UNSUPPORTED;
-        }
-    }
-    if (smem > 48 * 1024)
-        DSD_CU(cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-    int per_sm = 0;
-    DSD_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, kPeelThreads, smem));
-    if (per_sm <= 0) {
-        set_error("peel kernel does not fit on an SM (shared memory %zu bytes)", smem);
+    P.compact = h >= 3 ? 1 : 0;
+    if (h >= 5 && maxdplus > kBitmapMax) {
+        set_error("h=%d peeling needs at most %u higher-ranked neighbours per vertex "
+                  "(max here %u)", h, kBitmapMax, maxdplus);
         return DSD_ERR_UNSUPPORTED;
     }
-    if (per_sm > 4) per_sm = 4;
-    unsigned grid = (unsigned)(sms * per_sm);
+    // Shared memory: per-warp candidate buffers (h >= 3) or the big-item
+    // bitmap (h >= 5), then the small-regime alive list, frontier and
+    // neighbourhood bitmaps.  Block size: the largest whose candidate
+    // buffers leave room for the small-regime lists.
+    const size_t budget = 220 * 1024;
+    const size_t warp_words = (size_t)2 * P.cap + 32;
+    int NT = 1024;
+    if (h >= 3)
+        while (NT > 256 && (size_t)(NT / 32) * warp_words * 4 > budget / 2) NT >>= 1;
+    size_t work = h >= 3 ? (size_t)(NT / 32) * warp_words : 0;
+    if (h >= 5) {
+        size_t W = (P.cap + 31) / 32;
+        size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
+        if (big > work) work = big;
+    }
+    size_t room = budget > work * 4 + 12 * 1024 ? budget - work * 4 - 12 * 1024 : 0;
+    // per alive entry: list 4 B + frontier 4 B + one bit per bitmap slot
+    size_t per_entry_bits = 64 + (h >= 3 ? kBitmapSlots : 0);
+    size_t asmall = room * 8 / per_entry_bits;
+    asmall &= ~(size_t)31;
+    if (asmall > 16384) asmall = 16384;
+    if (asmall > peel_small_limit()) asmall = peel_small_limit() & ~31u;
+    if (asmall < 1024) asmall = 0;
+    // the jump combines one entry per block in a single pass over the threads
+    if (sms > NT || sms > 1024) asmall = 0;
+    P.work_words = (uint32_t)work;
+    P.asmall = (uint32_t)asmall;
+    size_t bm_words = h >= 3 ? (size_t)kBitmapSlots * (asmall / 32) : 0;
+    size_t smem = (work + 2 * asmall + bm_words) * 4;
 
-    uint8_t* state = nullptr;
+    uint32_t* sl = nullptr;
     uint32_t* lists = nullptr;
+    uint64_t* wmeta = nullptr;
+    uint32_t* wadj = nullptr;
     PeelCtrl* ctrl = nullptr;
     uint2* big = nullptr;
+    ulonglong2* jblk = nullptr;
     dsd_status st = DSD_OK;
     PeelCtrl hc;
+    unsigned grid = 0;
     cudaError_t e = cudaSuccess;
-    if ((st = dalloc(&state, n, s)) != DSD_OK) goto done;
-    if ((st = dalloc(&lists, (size_t)5 * n, s)) != DSD_OK) goto done;
+    const uint64_t nadj = 2 * g->m;   // both CSRs of g hold 2m entries
+    if ((st = dalloc(&sl, n, s)) != DSD_OK) goto done;
+    if ((st = dalloc(&lists, (size_t)6 * n, s)) != DSD_OK) goto done;
+    if ((st = dalloc(&jblk, 1024, s)) != DSD_OK) goto done;
+    if ((st = dalloc(&wmeta, (size_t)2 * n, s)) != DSD_OK) goto done;
+    if ((st = dalloc(&wadj, nadj + 1, s)) != DSD_OK) goto done;
     if ((st = dalloc(&ctrl, 1, s)) != DSD_OK) goto done;
     if (h >= 5) {
         P.big_cap = g->m * 2 + 1;
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
     }
-    P.state = state;
+    P.sl = sl;
     P.alive[0] = lists;
     P.alive[1] = lists + n;
     P.front[0] = lists + 2 * (size_t)n;
     P.front[1] = lists + 3 * (size_t)n;
     P.front[2] = lists + 4 * (size_t)n;
+    P.jf = lists + 5 * (size_t)n;
+    P.jblk = jblk;
+    P.wend = wmeta;
+    P.wnb = wmeta + n;
+    P.wadj = wadj;
     P.big = big;
     P.ctrl = ctrl;
     e = cudaMemsetAsync(ctrl, 0, sizeof(PeelCtrl), s);
+    if (e == cudaSuccess && nadj) e = cudaMemcpyAsync(wadj, adj, nadj * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
-        k_peel_init<<<sms * 4, 256, 0, s>>>(n, state, P.alive[0], ctrl); note_launch();
+        k_peel_init<<<sms * 4, 256, 0, s>>>(n, off, h >= 3 ? split : nullptr, sl, P.alive[0],
+                                            P.wend, P.wnb, ctrl);
+        note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        void* args[] = {&P};
-        e = cudaLaunchCooperativeKernel((void*)k_peel, dim3(grid), dim3(kPeelThreads), args,
-                                        smem, s);
-        note_launch();
+        if (NT == 1024) e = launch_peel<1024>(P, sms, smem, s, &grid);
+        else if (NT == 512) e = launch_peel<512>(P, sms, smem, s, &grid);
+        else e = launch_peel<256>(P, sms, smem, s, &grid);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(PeelCtrl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -700,11 +1219,21 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     res->rounds = hc.rounds;
     res->items = hc.items;
     res->bytes = hc.bytes;
+    res->barrier_ns = hc.barrier_ns;
+    res->barriers = hc.barriers;
+    res->compactions = hc.compactions;
+    res->threads = NT;
+    res->grid = grid;
+    res->small_round = hc.small_round;
+    for (int i = 0; i < 8; i++) res->tph[i] = hc.tph[i];
 done:
-    dev_free(state, s);
+    dev_free(sl, s);
     dev_free(lists, s);
+    dev_free(wmeta, s);
+    dev_free(wadj, s);
     dev_free(ctrl, s);
     dev_free(big, s);
+    dev_free(jblk, s);
     return st;
 }
 

@@ -157,6 +157,22 @@ def test_scaled_workloads(L, orc, name, hs):
     compare_all(L, orc, n, s, d, hs)
 
 
+@pytest.mark.parametrize("limit", [0, 1024, 3000])
+def test_peel_regimes(L, orc, limit):
+    """The peel's two round structures (global lists with several barriers
+    per round; alive set replicated in shared memory with one barrier) and
+    the switch between them give the same results."""
+    L.dsd_set_peel_small_limit(limit)
+    try:
+        n, s, d, _ = gg.workload("cl50k")
+        compare_all(L, orc, n, s, d, (2, 3, 4), csr=False)
+        for i in range(4):
+            n, s, d = gg.random_small(300, 0.08, seed=900 + i)
+            compare_all(L, orc, n, s, d, (2, 3, 5), csr=False)
+    finally:
+        L.dsd_set_peel_small_limit(16384)
+
+
 def test_er2000_bruteforce_subsamples(L, orc):
     """Configuration 1: 16-vertex induced subsamples against brute force."""
     import bruteforce as bf
