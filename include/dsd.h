@@ -181,6 +181,99 @@ typedef struct {
 dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
                         int mem, dsd_core_app_result* r);
 
+/* ------------------------------------------------------ learned proposal */
+
+/* Not in the paper: a small network proposes rho', a lower bound of the
+ * optimal h-clique density (Problem 1), from 64 statistics of the graph.
+ * The seeded call then decomposes only the (ceil(rho'),Psi)-core (Lemma 5;
+ * the clique-core bound of Sec. 5.2 limits it to an edge core) and falls
+ * back to the full decomposition when the proposal fails an exact test, so
+ * its outputs always equal dsd_core_app's.
+ *
+ * The network: 64 -> 256 -> 256 -> 256 -> 1, ReLU, BF16 weights with FP32
+ * master copy and accumulation, output log(1 + rho').  Training minimises the
+ * pinball (quantile) loss at quantile q with Adam (beta 0.9 / 0.999). */
+typedef struct dsd_model dsd_model;
+/* Number of parameters (148481). */
+uint64_t dsd_model_param_count(void);
+/* New model with deterministic He-uniform weights from `seed`. */
+dsd_status dsd_model_create(uint64_t seed, void* cuda_stream, dsd_model** out);
+void dsd_model_destroy(dsd_model* m);
+/* Parameters, Adam first and second moments, then the step count:
+ * state has 3 * count + 1 floats (host); count = dsd_model_param_count(). */
+dsd_status dsd_model_get_state(dsd_model* m, float* state, uint64_t count);
+dsd_status dsd_model_set_state(dsd_model* m, const float* state, uint64_t count);
+/* Network outputs for B <= 1024 feature rows X [B x 64] (host) into out [B] (host). */
+dsd_status dsd_model_forward(dsd_model* m, const float* X, uint32_t B, float* out);
+/* Mean pinball loss at quantile q on labels y [B] and its gradient with
+ * respect to the parameters (grad: count floats, host, may be NULL); no update. */
+dsd_status dsd_model_gradient(dsd_model* m, const float* X, const float* y, uint32_t B,
+                              float q, float* loss, float* grad);
+/* One Adam step (learning rate lr) on a batch; *loss (host, may be NULL) is
+ * the batch loss before the step. */
+dsd_status dsd_model_train_step(dsd_model* m, const float* X, const float* y, uint32_t B,
+                                float q, float lr, float* loss);
+/* The 64 statistics of g used as network input for clique size h: sizes,
+ * degree and edge-core histograms, and for three nested edge cores (all of
+ * V, core number >= degeneracy/2, core number = degeneracy) their sizes and
+ * clustering, triangle and h-clique estimates from neighbour pairs sampled
+ * around 4096 hashed vertices each.  Deterministic.  f: 64 floats, host or
+ * device memory as mem says. */
+dsd_status dsd_graph_features(dsd_graph* g, int h, float* f, int mem);
+
+typedef struct {
+    float rho_prime;          /* the proposal */
+    uint32_t accepted;        /* 1: answered from the (seed_k,Psi)-core */
+    uint64_t seed_k;          /* ceil(rho') */
+    uint64_t x0;              /* edge-core order the core was looked for in */
+    uint32_t sub_n;           /* vertices of that edge core */
+    uint32_t reserved;
+    uint64_t sub_m;           /* its edges */
+} dsd_seed_info;
+
+/* dsd_core_app with a proposal from model m: identical outputs (kmax_core,
+ * densest, r); r->nlevels counts the levels at or above seed_k when
+ * accepted.  info (may be NULL) describes what happened. */
+dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* m, uint32_t* kmax_core,
+                               uint32_t* densest, int mem, dsd_core_app_result* r,
+                               dsd_seed_info* info);
+
+/* ------------------------------------------------------------- batches */
+
+/* Many small graphs in one launch.  The paper treats one graph at a time;
+ * this runs the same path as dsd_graph_from_edges + dsd_core_app (CSR build,
+ * degeneracy peel, h-clique clique-degrees, (k,Psi)-core peel, CoreApp
+ * outputs) for every graph of a batch in one persistent kernel whose CTAs
+ * take graphs from a work queue (largest first), each graph handled by one
+ * CTA.  The launch is captured once in a CUDA graph and replayed by
+ * dsd_batch_run.
+ *   count graphs; graph i has n[i] vertices (<= 65535), clique size h[i]
+ *   (2..4) and m[i] edges: src/dst[e_i .. e_i + m[i]) with e_i the sum of
+ *   the earlier m (same clean-up rules as dsd_graph_from_edges).
+ *   mem: where src/dst live (copied at creation; the caller may free them).
+ *   want_cores != 0 keeps every graph's core numbers for dsd_batch_results.
+ *   autotune_cache: text file (may be NULL) remembering the launch shape
+ *   chosen for a batch signature; without an entry, creation times a few
+ *   shapes (threads per CTA, CTAs per SM) on the batch itself.
+ * Errors: DSD_ERR_INVALID, DSD_ERR_UNSUPPORTED (n, h or m out of range),
+ * DSD_ERR_NOMEM, DSD_ERR_CUDA. */
+typedef struct dsd_batch dsd_batch;
+dsd_status dsd_batch_create(uint32_t count, const uint32_t* n, const int* h, const uint64_t* m,
+                            const uint32_t* src, const uint32_t* dst, int mem, int want_cores,
+                            void* cuda_stream, const char* autotune_cache, dsd_batch** out);
+/* Run the whole batch once (one graph replay; asynchronous on the stream). */
+dsd_status dsd_batch_run(dsd_batch* b);
+/* Results of the last run (synchronises the stream).  res: count entries
+ * (the fields of dsd_core_app_result; kmax_core/densest sets are not kept);
+ * status: count entries, 0 ok, 1 invalid graph, 2 unsupported (h = 4 with
+ * more than 512 higher-ranked neighbours); cores: sum of n[i] entries in
+ * graph order, or NULL.  Any pointer may be NULL. */
+dsd_status dsd_batch_results(dsd_batch* b, dsd_core_app_result* res, int* status, uint64_t* cores);
+/* Chosen launch shape and its timed duration (ms, 0 if read from the cache). */
+dsd_status dsd_batch_info(const dsd_batch* b, uint32_t* threads, uint32_t* ctas_per_sm,
+                          float* tuned_ms);
+void dsd_batch_destroy(dsd_batch* b);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call; it exists for callers that

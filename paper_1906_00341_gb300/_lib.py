@@ -41,6 +41,15 @@ class CoreAppResult(ctypes.Structure):
                 ("nlevels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class SeedInfo(ctypes.Structure):
+    _fields_ = [("rho_prime", ctypes.c_float), ("accepted", ctypes.c_uint32),
+                ("seed_k", ctypes.c_uint64), ("x0", ctypes.c_uint64),
+                ("sub_n", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("sub_m", ctypes.c_uint64)]
+
+
+NFEAT = 64
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -66,10 +75,27 @@ SIGNATURES = {
     "dsd_core_decompose": (_int, [_P, _int, _P, _P, _int]),
     "dsd_level_stats": (_int, [_P, _int, _P, _P, _P, _u32, _P, _int]),
     "dsd_core_app": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult)]),
+    "dsd_batch_create": (_int, [_u32, _P, _P, _P, _P, _P, _int, _int, _P, ctypes.c_char_p,
+                                ctypes.POINTER(_P)]),
+    "dsd_batch_run": (_int, [_P]),
+    "dsd_batch_results": (_int, [_P, _P, _P, _P]),
+    "dsd_batch_info": (_int, [_P, _P, _P, _P]),
+    "dsd_batch_destroy": (None, [_P]),
     "dsd_triangle_degrees_noalloc": (_int, [_u32, _P, _P, _P, _P, _P]),
     "dsd_set_profiling": (_int, [_P, _int]),
     "dsd_phase_stats": (_int, [_P, _P, _P, _P]),
     "dsd_peel_stats": (_int, [_P, _int, _P]),
+    "dsd_model_param_count": (_u64, []),
+    "dsd_model_create": (_int, [_u64, _P, ctypes.POINTER(_P)]),
+    "dsd_model_destroy": (None, [_P]),
+    "dsd_model_get_state": (_int, [_P, _P, _u64]),
+    "dsd_model_set_state": (_int, [_P, _P, _u64]),
+    "dsd_model_forward": (_int, [_P, _P, _u32, _P]),
+    "dsd_model_gradient": (_int, [_P, _P, _P, _u32, ctypes.c_float, _P, _P]),
+    "dsd_model_train_step": (_int, [_P, _P, _P, _u32, ctypes.c_float, ctypes.c_float, _P]),
+    "dsd_graph_features": (_int, [_P, _int, _P, _int]),
+    "dsd_core_app_seeded": (_int, [_P, _int, _P, _P, _P, _int, ctypes.POINTER(CoreAppResult),
+                                   ctypes.POINTER(SeedInfo)]),
 }
 
 PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
@@ -180,6 +206,93 @@ def dsd_core_app(g, h, kcore_ptr, densest_ptr, mem):
     return r
 
 
+def dsd_batch_create(count, n_ptr, h_ptr, m_ptr, src_ptr, dst_ptr, mem, want_cores, stream_ptr,
+                     autotune_cache=None):
+    out = _P()
+    cache = autotune_cache.encode() if autotune_cache else None
+    _check(load().dsd_batch_create(count, n_ptr, h_ptr, m_ptr, src_ptr, dst_ptr, mem, want_cores,
+                                   stream_ptr, cache, ctypes.byref(out)))
+    return out.value
+
+
+def dsd_batch_run(b):
+    _check(load().dsd_batch_run(b))
+
+
+def dsd_batch_results(b, res_ptr, status_ptr, cores_ptr):
+    _check(load().dsd_batch_results(b, res_ptr, status_ptr, cores_ptr))
+
+
+def dsd_batch_info(b):
+    t = _u32()
+    c = _u32()
+    ms = ctypes.c_float()
+    _check(load().dsd_batch_info(b, ctypes.addressof(t), ctypes.addressof(c), ctypes.addressof(ms)))
+    return int(t.value), int(c.value), float(ms.value)
+
+
+def dsd_batch_destroy(b):
+    load().dsd_batch_destroy(b)
+
+
+class Batch:
+    """Many small graphs run by one persistent launch (captured in a CUDA
+    graph).  graphs: list of (n, src, dst, h) with numpy edge arrays."""
+
+    def __init__(self, graphs, want_cores=True, stream=None, autotune_cache=None):
+        self.count = len(graphs)
+        self.n = np.array([g[0] for g in graphs], np.uint32)
+        self.h = np.array([g[3] for g in graphs], np.int32)
+        self.m = np.array([len(g[1]) for g in graphs], np.uint64)
+        src = np.concatenate([np.asarray(g[1], np.uint32) for g in graphs]) if graphs else np.zeros(0, np.uint32)
+        dst = np.concatenate([np.asarray(g[2], np.uint32) for g in graphs]) if graphs else np.zeros(0, np.uint32)
+        self.src = np.ascontiguousarray(src)
+        self.dst = np.ascontiguousarray(dst)
+        self.want_cores = bool(want_cores)
+        sp = _stream_ptr(stream)
+        self.handle = dsd_batch_create(self.count, _np_ptr(self.n), _np_ptr(self.h), _np_ptr(self.m),
+                                       _np_ptr(self.src) if self.src.size else 0,
+                                       _np_ptr(self.dst) if self.dst.size else 0, DSD_MEM_HOST,
+                                       1 if want_cores else 0, sp, autotune_cache)
+
+    def run(self):
+        dsd_batch_run(self.handle)
+
+    def results(self):
+        res = (CoreAppResult * max(self.count, 1))()
+        status = np.zeros(max(self.count, 1), np.int32)
+        cores = np.zeros(max(int(self.n.sum()), 1), np.uint64) if self.want_cores else None
+        dsd_batch_results(self.handle, ctypes.addressof(res), _np_ptr(status),
+                          _np_ptr(cores) if cores is not None else 0)
+        out = []
+        pos = 0
+        for i in range(self.count):
+            r = res[i]
+            d = dict(kmax=int(r.kmax), kmax_core_size=int(r.kmax_core_size),
+                     kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                     densest_size=int(r.densest_size), densest_mu=int(r.densest_mu),
+                     nlevels=int(r.nlevels), status=int(status[i]))
+            if cores is not None:
+                d["core"] = cores[pos:pos + int(self.n[i])]
+            pos += int(self.n[i])
+            out.append(d)
+        return out
+
+    def info(self):
+        return dsd_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            dsd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dsd_triangle_degrees_noalloc(n, off_ptr, adj_ptr, deg_ptr, mu_ptr, stream_ptr):
     _check(load().dsd_triangle_degrees_noalloc(n, off_ptr, adj_ptr, deg_ptr, mu_ptr, stream_ptr))
 
@@ -201,6 +314,114 @@ def dsd_peel_stats(g, which):
     out = (ctypes.c_uint64 * len(PEEL_STATS))()
     _check(load().dsd_peel_stats(g, which, ctypes.addressof(out)))
     return dict(zip(PEEL_STATS, [int(x) for x in out]))
+
+
+def dsd_model_param_count():
+    return int(load().dsd_model_param_count())
+
+
+def dsd_model_create(seed, stream_ptr):
+    out = _P()
+    _check(load().dsd_model_create(seed, stream_ptr, ctypes.byref(out)))
+    return out.value
+
+
+def dsd_model_destroy(m):
+    load().dsd_model_destroy(m)
+
+
+def dsd_model_get_state(m, state_ptr, count):
+    _check(load().dsd_model_get_state(m, state_ptr, count))
+
+
+def dsd_model_set_state(m, state_ptr, count):
+    _check(load().dsd_model_set_state(m, state_ptr, count))
+
+
+def dsd_model_forward(m, x_ptr, B, out_ptr):
+    _check(load().dsd_model_forward(m, x_ptr, B, out_ptr))
+
+
+def dsd_model_gradient(m, x_ptr, y_ptr, B, q, loss_ptr, grad_ptr):
+    _check(load().dsd_model_gradient(m, x_ptr, y_ptr, B, q, loss_ptr, grad_ptr))
+
+
+def dsd_model_train_step(m, x_ptr, y_ptr, B, q, lr, loss_ptr):
+    _check(load().dsd_model_train_step(m, x_ptr, y_ptr, B, q, lr, loss_ptr))
+
+
+def dsd_graph_features(g, h, f_ptr, mem):
+    _check(load().dsd_graph_features(g, h, f_ptr, mem))
+
+
+def dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem):
+    r = CoreAppResult()
+    info = SeedInfo()
+    _check(load().dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem, ctypes.byref(r),
+                                      ctypes.byref(info)))
+    return r, info
+
+
+class Model:
+    """Owns one dsd_model handle (the density-proposal network).  Inputs and
+    outputs are float32 numpy arrays; the arithmetic runs in libdsd."""
+
+    def __init__(self, seed=0, stream=None):
+        self.stream_ptr = _stream_ptr(stream)
+        self.handle = dsd_model_create(seed, self.stream_ptr)
+        self.count = dsd_model_param_count()
+
+    def close(self):
+        if self.handle:
+            dsd_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state(self):
+        st = np.zeros(3 * self.count + 1, np.float32)
+        dsd_model_get_state(self.handle, _np_ptr(st), self.count)
+        return st
+
+    def set_state(self, st):
+        st = np.ascontiguousarray(st, np.float32)
+        if st.size != 3 * self.count + 1:
+            raise ValueError("state has %d floats, expected %d" % (st.size, 3 * self.count + 1))
+        dsd_model_set_state(self.handle, _np_ptr(st), self.count)
+
+    @staticmethod
+    def _x(X):
+        X = np.ascontiguousarray(X, np.float32)
+        if X.ndim != 2 or X.shape[1] != NFEAT:
+            raise ValueError("features must be B x %d" % NFEAT)
+        return X
+
+    def forward(self, X):
+        X = self._x(X)
+        out = np.zeros(max(X.shape[0], 1), np.float32)
+        dsd_model_forward(self.handle, _np_ptr(X), X.shape[0], _np_ptr(out))
+        return out[: X.shape[0]]
+
+    def gradient(self, X, y, q):
+        X = self._x(X)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = np.zeros(1, np.float32)
+        grad = np.zeros(self.count, np.float32)
+        dsd_model_gradient(self.handle, _np_ptr(X), _np_ptr(y), X.shape[0], q, _np_ptr(loss),
+                           _np_ptr(grad))
+        return float(loss[0]), grad
+
+    def train_step(self, X, y, q, lr):
+        X = self._x(X)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = np.zeros(1, np.float32)
+        dsd_model_train_step(self.handle, _np_ptr(X), _np_ptr(y), X.shape[0], q, lr,
+                             _np_ptr(loss))
+        return float(loss[0])
 
 
 # -------------------------------------------------------- convenience
@@ -345,6 +566,27 @@ class Graph:
         if sets:
             out["kmax_core"] = kc[: r.kmax_core_size]
             out["densest"] = de[: r.densest_size]
+        return out
+
+    def features(self, h):
+        f = np.zeros(NFEAT, np.float32)
+        dsd_graph_features(self.handle, h, _np_ptr(f), DSD_MEM_HOST)
+        return f
+
+    def core_app_seeded(self, h, model, mem="host", sets=True):
+        kc = self._alloc(self.n, 4, mem) if sets else None
+        de = self._alloc(self.n, 4, mem) if sets else None
+        r, info = dsd_core_app_seeded(self.handle, h, model.handle, self._ptr(kc) if sets else 0,
+                                      self._ptr(de) if sets else 0, self._memc(mem))
+        out = dict(kmax=int(r.kmax), kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                   densest_mu=int(r.densest_mu), densest_size=int(r.densest_size),
+                   kmax_core_size=int(r.kmax_core_size), nlevels=int(r.nlevels))
+        if sets:
+            out["kmax_core"] = kc[: r.kmax_core_size]
+            out["densest"] = de[: r.densest_size]
+        out["seed"] = dict(rho_prime=float(info.rho_prime), accepted=int(info.accepted),
+                           seed_k=int(info.seed_k), x0=int(info.x0), sub_n=int(info.sub_n),
+                           sub_m=int(info.sub_m))
         return out
 
     def set_profiling(self, on=True):

@@ -37,7 +37,8 @@ def _sources():
 
 
 def _headers():
-    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc"))
+            + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def _stale(target, deps):

@@ -28,9 +28,10 @@ constexpr uint32_t kBitmapMax = 1024;   // candidates per bitmap problem
 // search in C.
 
 // Warp builds one-word rows for |C| <= 32 (rows[i] for i < nc).
+template <class OFF>
 __device__ __forceinline__ void warp_build_rows32(const uint32_t* C, uint32_t nc,
-                                                  const uint64_t* ne, const uint32_t* adj,
-                                                  const uint64_t* nb, uint32_t* rows) {
+                                                  const OFF* ne, const uint32_t* adj,
+                                                  const OFF* nb, uint32_t* rows) {
     unsigned lane = lane_id();
     for (uint32_t i = 0; i < nc; i++) {
         uint32_t x = C[i];
@@ -104,9 +105,10 @@ __device__ __forceinline__ unsigned long long warp_dfs32(const uint32_t* rows, u
 // ---------------------------------------------------------------------------
 // Block-level bitmap routines for 32 < |C| <= 1024.  rows: nc * W words in
 // shared memory (W = ceil(nc/32)), zeroed by the caller.
+template <class OFF>
 __device__ __forceinline__ void block_build_rows(const uint32_t* C, uint32_t nc, uint32_t W,
-                                                 const uint64_t* ne, const uint32_t* adj,
-                                                 const uint64_t* nb, uint32_t* rows) {
+                                                 const OFF* ne, const uint32_t* adj,
+                                                 const OFF* nb, uint32_t* rows) {
     unsigned lane = lane_id();
     unsigned nw = blockDim.x >> 5;
     for (uint32_t i = warp_id(); i < nc; i += nw) {

@@ -1,4 +1,4 @@
-// K4: h-clique clique-degrees (Def. 3) and mu (Def. 4) over the
+// h-clique clique-degrees (Def. 3) and mu (Def. 4) over the
 // degeneracy-oriented graph.
 //
 // Every h-clique is listed once, from its lowest-ranked vertex u: it is u

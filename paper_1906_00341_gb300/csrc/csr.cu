@@ -1,4 +1,4 @@
-// K1: edge list -> cleaned symmetric CSR (Sec. 2 data model: undirected,
+// Edge list -> cleaned symmetric CSR (Sec. 2 data model: undirected,
 // unweighted, simple).  Counting pass, exclusive scan, scatter by atomic
 // cursors, per-row sort + unique, scan of the unique counts, row copy.
 #include "graph.cuh"

@@ -64,18 +64,18 @@ struct dsd_graph {
 
 namespace dsd {
 
-// CSR construction (K1).  src/dst on the device.
+// CSR construction.  src/dst on the device.
 dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32_t* dst);
 
-// Degeneracy order + relabelled CSR (K2 + K3), cached on g.
+// Degeneracy order + relabelled CSR, cached on g.
 dsd_status ensure_order(dsd_graph* g);
 
-// K4 on the relabelled graph: deg_new[rank] and *mu_dev (device pointers).
+// h-clique counting on the relabelled graph: deg_new[rank] and *mu_dev (device pointers).
 dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
                          unsigned long long* mu_dev);
 dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out);
 
-// Level-synchronous (k,Psi)-core peeling (K5/K6).
+// Level-synchronous (k,Psi)-core peeling.
 struct PeelResult {
     uint64_t kmax = 0;
     uint32_t nlevels = 0;
@@ -96,7 +96,12 @@ struct PeelResult {
 dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const uint32_t* adj,
                     const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
                     uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
-                    uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res);
+                    uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res,
+                    uint64_t kstart = 0);
+// kstart > 0: the first level removes every vertex with fewer than kstart
+// cliques in one cascade (threshold pruning to the (kstart,Psi)-core); its
+// level record is then (kstart - 1, |V|, mu) and the core numbers it assigns
+// are not core numbers.  Levels at or above kstart are exact.
 
 // Statistics of the last peel runs: [0] degeneracy peel, [1] (k,Psi) peel.
 void record_peel(dsd_graph* g, int which, const PeelResult& r);

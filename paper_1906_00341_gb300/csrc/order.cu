@@ -1,6 +1,6 @@
-// K2 + K3: degeneracy order and orientation.
+// Degeneracy order and orientation.
 //
-// K2 runs the level-synchronous peel with h = 2, which yields the edge
+// The first stage runs the level-synchronous peel with h = 2, which yields the edge
 // k-core numbers (Def. 5; the h = 2 case of the decomposition) and the round
 // in which each vertex left.  Vertices are then ranked by (round, id): a
 // vertex removed at level k had at most k alive neighbours, all of which are
@@ -9,7 +9,7 @@
 // The core-number bound gamma(v) = C(core_2(v), h-1) used by CoreApp
 // (Sec. 5.2) rests on the same core numbers.
 //
-// K3 relabels vertices by rank and rebuilds the CSR with sorted rows, so that
+// The second stage relabels vertices by rank and rebuilds the CSR with sorted rows, so that
 // N+(v) = {u in N(v) : u > v} is the tail of row v (start kept in rsplit).
 #include "graph.cuh"
 
@@ -126,7 +126,7 @@ dsd_status ensure_order(dsd_graph* g) {
         g->ordered = true;
         goto done;
     }
-    // K2: edge core numbers and removal rounds
+    // edge core numbers and removal rounds
     prof_begin(g, kPhaseOrderPeel);
     k_row_lengths<<<grid, 256, 0, s>>>(n, g->off, deg); note_launch();
     CUSTEP(cudaGetLastError());
@@ -141,7 +141,7 @@ dsd_status ensure_order(dsd_graph* g) {
     record_peel(g, 0, pr);
     R = pr.rounds + 1;
 
-    // K3: rank by (round, id), relabel, rebuild rows
+    // rank by (round, id), relabel, rebuild rows
     prof_begin(g, kPhaseOrient);
     STEP(dalloc(&hist, (size_t)R + 1, s));
     STEP(dalloc(&start, (size_t)R + 1, s));

@@ -1,4 +1,4 @@
-// K5/K6: level-synchronous (k,Psi)-core peeling with level statistics.
+// Level-synchronous (k,Psi)-core peeling with level statistics.
 //
 // Algorithm 3 removes one minimum clique-degree vertex at a time and lowers
 // the clique-degree of every vertex sharing a clique instance with it, never
@@ -120,6 +120,7 @@ struct PeelParams {
     PeelCtrl* ctrl;
     uint64_t wait_ns;
     unsigned long long mu0;
+    unsigned long long k0; // initial level: kstart - 1, or 0
     uint32_t cap;          // per-warp candidate buffer entries (>= max |N+|, >= 32)
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
     const uint32_t bm_words = (P.asmall + 31) / 32;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
 
-    unsigned long long k = 0;
+    unsigned long long k = P.k0;           // level floor (threshold pruning when > 0)
     unsigned long long mu_alive = P.mu0;   // meaningful in block 0
     uint32_t r = 0, jumps = 0, nlev = 0, nbar = 0, ncompact = 0;
     int ap = 0;
@@ -1093,7 +1094,8 @@ cudaError_t launch_peel(PeelParams& P, int sms, size_t smem, cudaStream_t s, uns
 dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const uint32_t* adj,
                     const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
                     uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
-                    uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res) {
+                    uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res,
+                    uint64_t kstart) {
     cudaStream_t s = g->stream;
     *res = PeelResult();
     if (n == 0) return DSD_OK;
@@ -1112,6 +1114,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.lvl_mu = lvl_mu;
     P.wait_ns = wait_limit_ns();
     P.mu0 = mu0;
+    P.k0 = kstart ? kstart - 1 : 0;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
     P.compact = h >= 3 ? 1 : 0;
     if (h >= 5 && maxdplus > kBitmapMax) {

@@ -21,6 +21,7 @@ const char* last_error() { return g_last_error; }
 
 dsd_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    (void)cudaGetLastError();   // a non-sticky error must not surface in a later check
     if (e == cudaErrorMemoryAllocation) return DSD_ERR_NOMEM;
     return DSD_ERR_CUDA;
 }

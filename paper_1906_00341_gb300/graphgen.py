@@ -246,3 +246,88 @@ def workload(name: str):
 
 
 WORKLOADS = ("er2000", "cl1m", "cl50k", "rmat22", "rmat14", "cl4m")
+
+
+# ---------------------------------------------------------------------------
+# Batches of small graphs.  Graph i: seed s_i = splitmix64(1000 + i) (the
+# standard 64-bit SplitMix constants), n = clamp(round(exp(N(ln 2000, 1.1^2))),
+# 50, 50000); type i mod 3: ER with average degree U[8, 32]; Chung-Lu with
+# exponent U[2.0, 2.5] and average degree U[8, 32]; ER background (average
+# degree U[8, 32]) plus a planted G(k, 0.6), k uniform in 10..100 (capped at
+# n); clique size h uniform in {2, 3, 4}.
+# ---------------------------------------------------------------------------
+
+def splitmix64(x: int) -> int:
+    x = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def batch_graph(i: int, nmax: int = 50000, nmedian: float = 2000.0):
+    """Graph i of the mixed batch: (n, src, dst, h)."""
+    seed = splitmix64(1000 + i)
+    rng = np.random.default_rng(seed)
+    n = int(min(max(round(math.exp(rng.normal(math.log(nmedian), 1.1))), 50), nmax))
+    avg = float(rng.uniform(8.0, 32.0))
+    h = int(rng.integers(2, 5))
+    kind = i % 3
+    sub = int(rng.integers(0, 2**31))
+    if kind == 0:
+        _, s, d = er(n, min(1.0, avg / max(n - 1, 1)), sub)
+    elif kind == 1:
+        beta = float(rng.uniform(2.0, 2.5))
+        draws = max(1, int(avg * n / 2))
+        wmax = max(2.0, math.sqrt(avg * n))
+        _, s, d = chung_lu(n, draws, beta, wmax, sub)
+    else:
+        _, s, d = er(n, min(1.0, avg / max(n - 1, 1)), sub)
+        k = int(min(rng.integers(10, 101), n))
+        _, s, d, _ = plant(n, s, d, k, 0.6, sub + 1)
+    return n, s, d, h
+
+
+def batch(count: int = 4096, nmax: int = 50000, nmedian: float = 2000.0):
+    return [batch_graph(i, nmax, nmedian) for i in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# Training graphs for the density proposal.  Graph i: seed
+# splitmix64(2,000,000 + i) (disjoint from the batch seeds and from the named
+# workloads), n = clamp(round(exp(N(ln 3000, 1.2^2))), 50, nmax); type i mod 4:
+# ER with average degree U[8, 32]; Chung-Lu with exponent U[2.0, 2.5] and
+# average degree U[8, 32]; ER background plus a planted G(k, U[0.4, 0.8]),
+# k uniform in 10..150; Chung-Lu background plus 1-5 planted G(k, U[0.3, 0.7])
+# blocks on disjoint vertices, k uniform in 20..300 (the shape of the
+# cl4m workload).  Clique size h = 3.
+# ---------------------------------------------------------------------------
+
+def train_graph(i: int, nmax: int = 200000, nmedian: float = 3000.0):
+    """Training graph i: (n, src, dst, h)."""
+    seed = splitmix64(2_000_000 + i)
+    rng = np.random.default_rng(seed)
+    n = int(min(max(round(math.exp(rng.normal(math.log(nmedian), 1.2))), 50), nmax))
+    avg = float(rng.uniform(8.0, 32.0))
+    kind = i % 4
+    sub = int(rng.integers(0, 2**31))
+    if kind in (0, 2):
+        _, s, d = er(n, min(1.0, avg / max(n - 1, 1)), sub)
+    else:
+        beta = float(rng.uniform(2.0, 2.5))
+        draws = max(1, int(avg * n / 2))
+        wmax = max(2.0, math.sqrt(avg * n))
+        _, s, d = chung_lu(n, draws, beta, wmax, sub)
+    if kind == 2:
+        k = int(min(rng.integers(10, 151), n))
+        _, s, d, _ = plant(n, s, d, k, float(rng.uniform(0.4, 0.8)), sub + 1)
+    elif kind == 3:
+        used = []
+        for j in range(int(rng.integers(1, 6))):
+            k = int(min(rng.integers(20, 301), n - len(used)))
+            if k < 3:
+                break
+            _, s, d, verts = plant(n, s, d, k, float(rng.uniform(0.3, 0.7)), sub + 1 + j,
+                                   exclude=used)
+            used.extend(verts.tolist())
+    return n, s, d, 3

@@ -1,0 +1,101 @@
+"""Batched executor: every graph of a mixed batch (uneven sizes, h in 2..4)
+run by the persistent launch must give exactly what the single-graph path
+gives (and, for a sample, what the oracle gives)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_1906_00341_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1906_00341_gb300 import build as b
+    b.build()
+    from paper_1906_00341_gb300 import _lib
+    _lib.load()
+    return _lib
+
+
+def single(L, n, s, d, h):
+    with L.Graph.from_edges(n, s, d) as g:
+        r = g.core_app(h, sets=False)
+        core, kmax = g.core_decompose(h)
+    return r, core
+
+
+def check_batch(L, graphs, orc=None, oracle_every=0):
+    b = L.Batch(graphs, want_cores=True)
+    b.run()
+    res = b.results()
+    for i, ((n, s, d, h), r) in enumerate(zip(graphs, res)):
+        assert r["status"] == 0, (i, r["status"])
+        want, wcore = single(L, n, s, d, h)
+        for key in ("kmax", "kmax_core_size", "kmax_core_mu", "best_k", "densest_size",
+                    "densest_mu", "nlevels"):
+            assert r[key] == want[key], (i, n, h, key, r[key], want[key])
+        assert np.array_equal(r["core"], wcore), (i, n, h)
+        if orc is not None and oracle_every and i % oracle_every == 0:
+            og = orc.csr(n, s, d)
+            ocore, ok = orc.core_decompose(og, h)
+            assert np.array_equal(r["core"], ocore) and r["kmax"] == ok
+    b.close()
+    return res
+
+
+def test_batch_mixed_small(L, orc):
+    graphs = gg.batch(48, nmax=3000, nmedian=400.0)
+    check_batch(L, graphs, orc, oracle_every=4)
+
+
+def test_batch_edge_cases(L):
+    e = np.zeros(0, np.uint32)
+    graphs = [
+        (1, e, e, 2),
+        (5, e, e, 3),                                                   # no edges
+        (3, np.array([0, 1, 1], np.uint32), np.array([0, 1, 2], np.uint32), 2),  # loops
+        (4, np.array([0, 0, 0, 1, 1, 2], np.uint32), np.array([1, 2, 3, 2, 3, 3], np.uint32), 4),
+        (60, *np.triu_indices(60, 1), 3),                             # K_60
+    ]
+    graphs = [(n, np.asarray(s, np.uint32), np.asarray(d, np.uint32), h) for n, s, d, h in graphs]
+    check_batch(L, graphs)
+
+
+def test_batch_rejects_and_flags(L):
+    with pytest.raises(L.DSDError) as ei:
+        L.Batch([(70000, np.zeros(0, np.uint32), np.zeros(0, np.uint32), 3)])
+    assert ei.value.name == "DSD_ERR_UNSUPPORTED"
+    # an endpoint out of range marks that graph invalid, the others still run
+    good = gg.batch_graph(1, nmax=500, nmedian=200.0)
+    bad = (10, np.array([0, 11], np.uint32), np.array([1, 2], np.uint32), 3)
+    b = L.Batch([good, bad])
+    b.run()
+    res = b.results()
+    assert res[0]["status"] == 0 and res[1]["status"] == 1
+    b.close()
+
+
+def test_batch_autotune_cache(L, tmp_path):
+    graphs = gg.batch(24, nmax=2000, nmedian=300.0)
+    cache = str(tmp_path / "tune.txt")
+    b1 = L.Batch(graphs, want_cores=False, autotune_cache=cache)
+    t1 = b1.info()
+    b1.close()
+    assert os.path.exists(cache) and open(cache).read().count("|") == 1
+    b2 = L.Batch(graphs, want_cores=False, autotune_cache=cache)
+    t2 = b2.info()
+    assert t1[:2] == t2[:2]
+    # replays of the captured graph give the same answers
+    b2.run()
+    r1 = b2.results()
+    b2.run()
+    r2 = b2.results()
+    assert r1 == r2
+    b2.close()
