@@ -10,7 +10,15 @@ the (k_max,Psi)-core, the densest level set with its exact density).
 
 Printed: one JSON line (rank 0).  value = h-cliques per second of device
 time per step (mu / step time); e2e = the same through the C ABI with host
-buffers (edge upload and result download inside the timed region).
+buffers (edge upload and result download inside the timed region).  Two
+more objects on the same line (rank 0, skipped with --no-learned /
+--no-batched):
+  learned -- the trained density proposal: dsd_core_app_seeded vs
+             dsd_core_app on the held-out Chung-Lu graph n = 4,000,000 (64M
+             draws, exponent 2.2, five planted G(300, 0.4)), h = 3: speedup,
+             acceptance rate, identical outputs;
+  batched -- 4096 mixed graphs (h in {2,3,4}) in one CUDA-graph replay of the
+             persistent batch kernel vs a host loop of the plain path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -37,7 +45,7 @@ H = 3
 L2_BYTES = 129 * 1024 * 1024
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -46,7 +54,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--h", type=int, default=H)
-    return ap.parse_args()
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-seeded vs plain leg (cl4m, h=3)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched leg (4096 mixed graphs)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--once", action="store_true",
+                    help="build the workload graph, run dsd_core_app once, print k_max and "
+                         "exit (a short command for kernel profiles)")
+    return ap.parse_args(argv)
 
 
 def dist_info():
@@ -54,6 +70,19 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value, world, device=None):
+    """The maximum of a per-rank float over all ranks (identity at world 1);
+    works with the nccl (CUDA tensor) and gloo (CPU tensor) backends."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -188,12 +217,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = (L.dsd_kernel_launches() - launches0) // max(args.steps, 1)
-    t_ms = float(np.sum(times))
+    t_ms = max_over_ranks(float(np.sum(times)), world, dev)
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
         dist.barrier()
     ms_per_step = t_ms / args.steps
     value = world * mu / (ms_per_step / 1e3)
@@ -263,6 +289,179 @@ def run_ours(args, rank, world, local):
     return line, (n, s, d, h, mu)
 
 
+# ----------------------------------------------------- learned proposal
+
+def run_learned(args, local):
+    """Seeded (trained proposal) vs plain CoreApp on the held-out Chung-Lu
+    graph n = 4,000,000, 64,000,000 draws, exponent 2.2, five planted
+    G(300, 0.4) blocks, h = 3: device time per call (CSR build included in
+    both), identical outputs required."""
+    import torch
+    from paper_1906_00341_gb300 import graphgen as gg
+    from paper_1906_00341_gb300 import _lib as L
+    from paper_1906_00341_gb300 import train
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    ck = train.DEFAULT_CHECKPOINT
+    if not os.path.exists(ck):
+        return {"unavailable": "no trained checkpoint at %s" % os.path.relpath(ck, ROOT)}
+    M = train.load_checkpoint(ck)
+    untrained = L.Model(seed=1)
+    n, s, d, _ = gg.workload("cl4m")
+    h = 3
+    src = torch.from_numpy(s.astype(np.int32)).to(dev)
+    dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+    kc = torch.empty(n, dtype=torch.int32, device=dev)
+    de = torch.empty(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def call(model):
+        g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE, sp)
+        if model is None:
+            r = L.dsd_core_app(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
+            info = None
+        else:
+            r, info = L.dsd_core_app_seeded(g, h, model.handle, kc.data_ptr(), de.data_ptr(),
+                                            L.DSD_MEM_DEVICE)
+        return g, r, info
+
+    def answer(r):
+        return (int(r.kmax), int(r.kmax_core_size), int(r.kmax_core_mu), int(r.best_k),
+                int(r.densest_mu), int(r.densest_size),
+                kc[: r.kmax_core_size].cpu().numpy().tobytes(),
+                de[: r.densest_size].cpu().numpy().tobytes())
+
+    out = {}
+    ref = None
+    for name, model in (("plain", None), ("seeded", M), ("untrained", untrained)):
+        for _ in range(args.warmup):
+            g, r, info = call(model)
+            L.dsd_graph_destroy(g)
+        times, acc, same = [], [], True
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g, r, info = call(model)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            a = answer(r)
+            if ref is None:
+                ref = a
+            same = same and a == ref
+            if info is not None:
+                acc.append(int(info.accepted))
+            L.dsd_graph_destroy(g)
+        rec = {"ms": float(np.mean(times)), "identical": bool(same)}
+        if info is not None:
+            rec.update(accepted=float(np.mean(acc)), rho_prime=float(info.rho_prime),
+                       seed_k=int(info.seed_k), x0=int(info.x0), sub_n=int(info.sub_n),
+                       sub_m=int(info.sub_m))
+        out[name] = rec
+    torch.cuda.synchronize()
+    return {
+        "workload": "chung_lu n=4e6 draws=6.4e7 beta=2.2 wmax=sqrt(1.28e8) + 5 x G(300,0.4), h=3",
+        "checkpoint": M.header.get("sha256", "")[:16],
+        "train_graphs": M.header.get("meta", {}).get("graphs"),
+        "speedup": out["plain"]["ms"] / out["seeded"]["ms"],
+        "acceptance_rate": out["seeded"]["accepted"],
+        "identical_output": out["seeded"]["identical"] and out["untrained"]["identical"],
+        "densest": [int(ref[4]), int(ref[5])], "kmax": int(ref[0]),
+        "plain": out["plain"], "seeded": out["seeded"], "untrained": out["untrained"],
+        "timing": "CUDA events per call (CSR build + decomposition), mean of %d after %d "
+                  "warm-up, L2 flushed between calls" % (args.steps, args.warmup),
+    }
+
+
+# ------------------------------------------------------------- batched
+
+def _batch_graph(i):
+    from paper_1906_00341_gb300 import graphgen as gg
+    return gg.batch_graph(i)
+
+
+def make_batch(count, workers=8):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_graph, range(count), 32)
+
+
+def run_batched(args, local, graphs):
+    """graphs/s of one CUDA-graph replay of the persistent batch kernel vs a
+    host loop that runs the plain path (dsd_graph_from_edges +
+    dsd_core_app, device-resident edges) once per graph."""
+    import torch
+    from paper_1906_00341_gb300 import _lib as L
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    cache = os.path.join(ROOT, "gpurun_out", "batch_autotune.txt")
+    B = L.Batch(graphs, want_cores=False, stream=stream, autotune_cache=cache)
+    threads, cps, tuned = B.info()
+    for _ in range(args.warmup):
+        B.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.run()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    res = B.results()
+    ok = sum(1 for r in res if r["status"] == 0)
+    batch_ms = float(np.mean(times))
+    # the loop: every 8th graph (a fixed, size-representative subset), scaled
+    sub = list(range(0, len(graphs), 8))
+    src = [torch.from_numpy(np.asarray(graphs[i][1], np.int32)).to(dev) for i in sub]
+    dst = [torch.from_numpy(np.asarray(graphs[i][2], np.int32)).to(dev) for i in sub]
+    nmax = max(int(graphs[i][0]) for i in sub)
+    kc = torch.empty(nmax, dtype=torch.int32, device=dev)
+    de = torch.empty(nmax, dtype=torch.int32, device=dev)
+    mismatch = 0
+
+    def loop(check):
+        nonlocal mismatch
+        for j, i in enumerate(sub):
+            n, _, _, h = graphs[i]
+            g = L.dsd_graph_from_edges(n, src[j].numel(), src[j].data_ptr(), dst[j].data_ptr(),
+                                       L.DSD_MEM_DEVICE, sp)
+            r = L.dsd_core_app(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
+            L.dsd_graph_destroy(g)
+            if check:
+                b = res[i]
+                if (int(r.kmax), int(r.best_k), int(r.densest_mu), int(r.densest_size)) != \
+                        (b["kmax"], b["best_k"], b["densest_mu"], b["densest_size"]):
+                    mismatch += 1
+
+    loop(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    loop(False)
+    e1.record(stream)
+    e1.synchronize()
+    loop_ms = e0.elapsed_time(e1) * len(graphs) / len(sub)
+    B.close()
+    return {
+        "workload": "%d graphs: n lognormal (median 2000, sigma 1.1) in [50, 50000], "
+                    "1/3 ER, 1/3 Chung-Lu, 1/3 ER + planted G(k,0.6); h in {2,3,4}" % len(graphs),
+        "graphs_per_s": len(graphs) / (batch_ms / 1e3), "batch_ms": batch_ms,
+        "loop_graphs_per_s": len(graphs) / (loop_ms / 1e3), "loop_ms": loop_ms,
+        "speedup": loop_ms / batch_ms, "graphs_ok": ok,
+        "loop_mismatches": mismatch, "loop_sample": len(sub),
+        "autotuned": {"threads": int(threads), "ctas_per_sm": int(cps), "ms": float(tuned)},
+        "timing": "CUDA events; batch: mean of %d replays after %d; loop: one pass over every "
+                  "8th graph after a checked pass, scaled to the batch" % (args.steps, args.warmup),
+    }
+
+
 # ------------------------------------------------------------- CPU side
 
 def cpu_sample(n, s, d, frac=0.5, seed=99):
@@ -311,19 +510,48 @@ def run_reference(args, rank, world):
     }
 
 
+def run_once(args, local):
+    import torch
+    from paper_1906_00341_gb300 import graphgen as gg
+    from paper_1906_00341_gb300 import _lib as L
+    L.load()
+    dev = torch.device("cuda", local)
+    n, s, d, _ = gg.workload(args.workload)
+    src = torch.from_numpy(s.astype(np.int32)).to(dev)
+    dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE, sp)
+    r = L.dsd_core_app(g, args.h, 0, 0, L.DSD_MEM_HOST)
+    L.dsd_graph_destroy(g)
+    print(json.dumps({"workload": args.workload, "h": args.h, "kmax": int(r.kmax),
+                      "best_k": int(r.best_k), "densest": [int(r.densest_mu),
+                                                           int(r.densest_size)]}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
+    if args.once:
+        if rank == 0:
+            run_once(args, local)
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0
         print(json.dumps(run_reference(args, rank, world)), flush=True)
         return 0
+    graphs = None
+    if not args.no_batched and rank == 0:
+        graphs = make_batch(args.batch_count)   # host processes, before any CUDA call
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     line, (n, s, d, h, mu) = run_ours(args, rank, world, local)
     if rank == 0:
+        if not args.no_learned:
+            line["learned"] = run_learned(args, local)
+        if graphs is not None:
+            line["batched"] = run_batched(args, local, graphs)
         if not args.no_cpu_baseline and world == 1:
             ns, ss, ds = cpu_sample(n, s, d)
             t, smu, _ = time_oracle(ns, ss, ds, h)

@@ -181,6 +181,16 @@ typedef struct {
 dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
                         int mem, dsd_core_app_result* r);
 
+/* ---------------------------------------------------- failure detection */
+
+/* Runs the grid barrier of the peeling kernel (one block per SM, bounded
+ * waits) on `cuda_stream`.  absent_block < 0: all blocks pass four barriers,
+ * DSD_OK.  absent_block = b >= 0: block b leaves without arriving, every
+ * other block's wait runs out after wait_ms (1..60000) and the call returns
+ * DSD_ERR_TIMEOUT; the kernel ends and the context stays usable.  The same
+ * limit (dsd_set_wait_limit_ms) turns a stalled peel into DSD_ERR_TIMEOUT. */
+dsd_status dsd_check_barrier_timeout(int absent_block, uint32_t wait_ms, void* cuda_stream);
+
 /* ------------------------------------------------------ learned proposal */
 
 /* Not in the paper: a small network proposes rho', a lower bound of the

@@ -85,6 +85,7 @@ SIGNATURES = {
     "dsd_set_profiling": (_int, [_P, _int]),
     "dsd_phase_stats": (_int, [_P, _P, _P, _P]),
     "dsd_peel_stats": (_int, [_P, _int, _P]),
+    "dsd_check_barrier_timeout": (_int, [_int, _u32, _P]),
     "dsd_model_param_count": (_u64, []),
     "dsd_model_create": (_int, [_u64, _P, ctypes.POINTER(_P)]),
     "dsd_model_destroy": (None, [_P]),
@@ -314,6 +315,10 @@ def dsd_peel_stats(g, which):
     out = (ctypes.c_uint64 * len(PEEL_STATS))()
     _check(load().dsd_peel_stats(g, which, ctypes.addressof(out)))
     return dict(zip(PEEL_STATS, [int(x) for x in out]))
+
+
+def dsd_check_barrier_timeout(absent_block, wait_ms, stream_ptr):
+    _check(load().dsd_check_barrier_timeout(absent_block, wait_ms, stream_ptr))
 
 
 def dsd_model_param_count():

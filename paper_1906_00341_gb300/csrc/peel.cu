@@ -1068,6 +1068,17 @@ __global__ void k_peel_init(uint32_t n, const uint64_t* off, const uint64_t* spl
     }
 }
 
+// Failure detection: the grid barrier of k_peel with one block withheld
+// (absent >= 0), so that every other block's bounded wait runs out and sets
+// the timeout flag; absent < 0 passes four barriers normally.
+__global__ void k_barrier_probe(PeelCtrl* c, uint64_t wait_ns, int absent) {
+    unsigned long long waited = 0;
+    if ((int)blockIdx.x == absent) return;
+    for (int i = 0; i < 4; i++)
+        if (!grid_barrier(c, wait_ns, waited)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->barriers = 4;
+}
+
 template <int NT>
 cudaError_t launch_peel(PeelParams& P, int sms, size_t smem, cudaStream_t s, unsigned* grid_out) {
     cudaError_t e = cudaSuccess;
@@ -1241,3 +1252,41 @@ done:
 }
 
 }  // namespace dsd
+
+extern "C" dsd_status dsd_check_barrier_timeout(int absent_block, uint32_t wait_ms,
+                                                void* cuda_stream) {
+    using namespace dsd;
+    set_error("");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int sms = 152;
+    DSD_TRY(num_sms(&sms));
+    if (wait_ms == 0 || wait_ms > 60000 || absent_block >= sms) {
+        set_error("dsd_check_barrier_timeout: need 0 < wait_ms <= 60000 and absent_block < %d",
+                  sms);
+        return DSD_ERR_INVALID;
+    }
+    PeelCtrl* ctrl = nullptr;
+    DSD_TRY(dalloc(&ctrl, 1, s));
+    PeelCtrl hc;
+    memset(&hc, 0, sizeof(hc));
+    uint64_t wait_ns = (uint64_t)wait_ms * 1000000ull;
+    int absent = absent_block;
+    void* args[] = {&ctrl, &wait_ns, &absent};
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(PeelCtrl), s);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((void*)k_barrier_probe, dim3(sms), dim3(128), args, 0, s);
+    note_launch();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(ctrl, s);
+    if (e != cudaSuccess) return cuda_fail(e, "barrier probe", __FILE__, __LINE__);
+    if (hc.error & kErrTimeout) {
+        set_error("grid barrier wait ran out after %u ms (block %d withheld)", wait_ms, absent);
+        return DSD_ERR_TIMEOUT;
+    }
+    if (hc.error || hc.barriers != 4) {
+        set_error("barrier probe: error %u, %u barriers", hc.error, hc.barriers);
+        return DSD_ERR_INTERNAL;
+    }
+    return DSD_OK;
+}
