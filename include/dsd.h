@@ -84,6 +84,11 @@ dsd_status dsd_set_wait_limit_ms(uint32_t ms);
  * 16384 (also capped by shared memory); 0 disables it.  Results do not
  * depend on it.  Process-wide; applies to calls started afterwards. */
 dsd_status dsd_set_peel_small_limit(uint32_t max_alive);
+/* Largest alive set whose remaining levels (h = 2, 3) are finished by one
+ * thread-block cluster holding the alive subgraph as bitmap rows in
+ * distributed shared memory (default: as large as the cluster holds, about
+ * 4,600 vertices; 0 = never).  Results do not depend on it.  Process-wide. */
+dsd_status dsd_set_peel_tail_limit(uint32_t max_alive);
 
 /* ---------------------------------------------------------------- graphs */
 
@@ -328,8 +333,12 @@ dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* l
  * every block's shared memory (0 if none), then block 0's time (ns) in each
  * phase outside barriers: [large regime] retire/mark, alive-list scan, level
  * jump, clique enumeration; [small regime] retire/copy, level jump,
- * mark/bitmaps, clique enumeration.  Zeros if that peel has not run. */
-#define DSD_PEEL_STATS 19
+ * mark/bitmaps, clique enumeration; then the alive vertices handed to the
+ * cluster tail kernel (0 if none), the round of the hand-over, the tail
+ * kernel's time (ns) and its lead CTA's time (ns) in: building the rows,
+ * frontier broadcast, level jumps and frontier lists, clique enumeration,
+ * retiring.  Zeros if that peel has not run. */
+#define DSD_PEEL_STATS 27
 dsd_status dsd_peel_stats(dsd_graph* g, int which, uint64_t* out);
 
 #ifdef __cplusplus

@@ -64,6 +64,7 @@ SIGNATURES = {
     "dsd_kernel_launches": (ctypes.c_uint64, []),
     "dsd_set_wait_limit_ms": (_int, [_u32]),
     "dsd_set_peel_small_limit": (_int, [_u32]),
+    "dsd_set_peel_tail_limit": (_int, [_u32]),
     "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_destroy": (None, [_P]),
@@ -102,7 +103,9 @@ SIGNATURES = {
 PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
               "threads", "grid", "kmax", "small_round",
               "t_large_retire", "t_large_scan", "t_large_jump", "t_large_enum",
-              "t_small_retire", "t_small_jump", "t_small_mark", "t_small_enum")
+              "t_small_retire", "t_small_jump", "t_small_mark", "t_small_enum",
+              "tail_n", "tail_round", "tail_ns",
+              "t_tail_build", "t_tail_front", "t_tail_jump", "t_tail_enum", "t_tail_retire")
 
 
 def load(path: str = LIB_PATH):
@@ -152,6 +155,10 @@ def dsd_set_wait_limit_ms(ms):
 
 def dsd_set_peel_small_limit(max_alive):
     _check(load().dsd_set_peel_small_limit(max_alive))
+
+
+def dsd_set_peel_tail_limit(max_alive):
+    _check(load().dsd_set_peel_tail_limit(max_alive))
 
 
 def dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr):

@@ -15,6 +15,9 @@ uint64_t wait_limit_ns() { return g_wait_ns; }
 static std::atomic<uint32_t> g_small_limit{16384};
 uint32_t peel_small_limit() { return g_small_limit.load(); }
 
+static std::atomic<uint32_t> g_tail_limit{1u << 30};
+uint32_t peel_tail_limit() { return g_tail_limit.load(); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -32,6 +35,10 @@ void record_peel(dsd_graph* g, int which, const PeelResult& r) {
     o[9] = r.kmax;
     o[10] = r.small_round;
     for (int i = 0; i < 8; i++) o[11 + i] = r.tph[i];
+    o[19] = r.tail_n;
+    o[20] = r.tail_round;
+    o[21] = r.tail_ns;
+    for (int i = 0; i < 5; i++) o[22 + i] = r.tail_tph[i];
 }
 
 void prof_begin(dsd_graph* g, int phase) {
@@ -336,6 +343,11 @@ dsd_status dsd_set_wait_limit_ms(uint32_t ms) {
 
 dsd_status dsd_set_peel_small_limit(uint32_t max_alive) {
     g_small_limit = max_alive;
+    return DSD_OK;
+}
+
+dsd_status dsd_set_peel_tail_limit(uint32_t max_alive) {
+    g_tail_limit = max_alive;
     return DSD_OK;
 }
 

@@ -54,6 +54,8 @@ void note_launch();
 
 // Largest alive set the peel replicates in every block's shared memory.
 uint32_t peel_small_limit();
+// Largest alive set handed to the cluster tail kernel (0 = never).
+uint32_t peel_tail_limit();
 
 // --------------------------------------------------------- device utils
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -47,6 +47,7 @@
 #include "cliques.cuh"
 #include "graph.cuh"
 
+#include <cooperative_groups.h>
 #include <string.h>
 
 namespace dsd {
@@ -85,6 +86,16 @@ struct PeelCtrl {
     uint32_t small_round;           // first round of the small regime (0 = never)
     uint32_t pad3;
     unsigned long long tph[8];      // block 0's time per phase (ns)
+    // hand-over to the cluster tail kernel
+    uint32_t tail_n;                // alive vertices handed over (0 = none)
+    uint32_t tail_round;            // round at the hand-over
+    uint32_t tail_sel;              // which hand-over list holds them
+    uint32_t tail_entry;            // alive vertices at the first hand-over
+    uint32_t tail_entry_round;      // its round
+    uint32_t pad4;
+    unsigned long long mu_tail;     // mu of the alive graph at the hand-over
+    unsigned long long tail_ns;     // the tail kernel's duration
+    unsigned long long tail_tph[5]; // tail CTA 0's time: build, A+sync, jump+list, C+sync, D
 };
 
 // Byte meter.  Every global-memory element the algorithm reads or writes is
@@ -125,6 +136,7 @@ struct PeelParams {
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
     uint32_t asmall;       // small-regime list capacity (0 = regime off)
+    uint32_t tail_max;     // hand over to the cluster tail at <= this many alive (0 = off)
 };
 
 // ------------------------------------------------------------ barrier
@@ -973,6 +985,30 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 }
                 __syncthreads();
                 if (tot_alive == 0) break;
+                if (tot_alive <= P.tail_max) {
+                    // Hand the rest to the cluster tail kernel: every block
+                    // writes its compacted slice into one list (blocks in
+                    // order) and gives those vertices their tail local ids.
+                    uint32_t before_me = 0;
+                    if (threadIdx.x < gridDim.x && threadIdx.x < blockIdx.x)
+                        before_me = (uint32_t)(P.jblk[threadIdx.x].y >> 32);
+                    uint32_t base;
+                    block_scan_count<NT>(before_me, s_wtot, &base);
+                    for (uint32_t i = threadIdx.x; i < na_loc; i += NT) {
+                        uint32_t v = sA[i];
+                        P.alive[0][base + i] = v;
+                        P.sl[v] = ((base + i) << 2) | kAlive;
+                    }
+                    if (lead) {
+                        c->tail_n = (uint32_t)tot_alive;
+                        c->tail_round = r;
+                        c->tail_entry = (uint32_t)tot_alive;
+                        c->tail_entry_round = r;
+                        c->mu_tail = mu_alive;
+                        bytes += 12ull * tot_alive;
+                    }
+                    break;
+                }
                 k = gm > k ? gm : k;
                 na_s = (uint32_t)tot_alive;
                 if (lead) {
@@ -1068,6 +1104,92 @@ __global__ void k_peel_init(uint32_t n, const uint64_t* off, const uint64_t* spl
     }
 }
 
+#include "peel_tail.inc"
+
+// Tail launch shapes: the largest cluster this device co-schedules (16,
+// else 8) and the largest alive set whose per-CTA state fits its shared
+// memory; `grows` selects rows in global memory.
+struct TailShape {
+    uint32_t cs = 0, cap = 0;
+    size_t smem = 0;
+};
+
+TailShape find_tail_shape(bool grows) {
+    TailShape t;
+    const size_t budget = 220 * 1024;
+    const void* fn = grows ? (const void*)k_peel_tail<true> : (const void*)k_peel_tail<false>;
+    for (uint32_t cs : {16u, 8u}) {
+        uint32_t cap = 0;
+        for (uint32_t cc = 32 * cs; cc <= kTailMaxAlive; cc += 32 * cs) {
+            size_t scratch = grows ? SIZE_MAX : (size_t)(cc / cs) * (cc / 32) * 4;
+            if (tail_smem_bytes(grows, cc, cs) <= budget && tail_np(cc) * 4 <= scratch &&
+                (grows || cc <= 8192))
+                cap = cc;
+        }
+        if (!cap) continue;
+        size_t smem = tail_smem_bytes(grows, cap, cs);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            (cs > 8 &&
+             cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                 cudaSuccess)) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kTailNT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (nc >= 1) {
+            t.cs = cs;
+            t.cap = cap;
+            t.smem = smem;
+            break;
+        }
+    }
+    return t;
+}
+
+const TailShape& tail_shape(bool grows) {
+    static TailShape cached[2];
+    static bool done[2] = {false, false};
+    if (!done[grows]) {
+        cached[grows] = find_tail_shape(grows);
+        done[grows] = true;
+    }
+    return cached[grows];
+}
+
+template <bool GROWS>
+cudaError_t launch_tail(const TailParams& T, const TailShape& sh, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = sh.cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(sh.cs);
+    cfg.blockDim = dim3(kTailNT);
+    cfg.dynamicSmemBytes = sh.smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelEx(&cfg, k_peel_tail<GROWS>, T);
+}
+
 // Failure detection: the grid barrier of k_peel with one block withheld
 // (absent >= 0), so that every other block's bounded wait runs out and sets
 // the timeout flag; absent < 0 passes four barriers normally.
@@ -1160,6 +1282,17 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     if (sms > NT || sms > 1024) asmall = 0;
     P.work_words = (uint32_t)work;
     P.asmall = (uint32_t)asmall;
+    TailShape tsh_d, tsh_g;   // rows in distributed shared memory / in global memory
+    if ((h == 2 || h == 3) && asmall > 0 && peel_tail_limit() > 0) {
+        tsh_d = tail_shape(false);
+        // global rows pay for h = 3 only: an h = 2 round is too cheap for the
+        // wider rows (measured on the 1M-vertex Chung-Lu graph)
+        if (tsh_d.cs && h == 3) tsh_g = tail_shape(true);
+        uint32_t tmax = tsh_g.cs && tsh_g.cap > tsh_d.cap ? tsh_g.cap : tsh_d.cap;
+        if (tmax > peel_tail_limit()) tmax = peel_tail_limit();
+        if (tmax <= tsh_d.cap) tsh_g = TailShape();   // the global-row launch is not needed
+        if (tsh_d.cs) P.tail_max = tmax;
+    }
     size_t bm_words = h >= 3 ? (size_t)kBitmapSlots * (asmall / 32) : 0;
     size_t smem = (work + 2 * asmall + bm_words) * 4;
 
@@ -1168,6 +1301,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     uint64_t* wmeta = nullptr;
     uint32_t* wadj = nullptr;
     PeelCtrl* ctrl = nullptr;
+    uint32_t* rows_g = nullptr;
     uint2* big = nullptr;
     ulonglong2* jblk = nullptr;
     dsd_status st = DSD_OK;
@@ -1181,6 +1315,9 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     if ((st = dalloc(&wmeta, (size_t)2 * n, s)) != DSD_OK) goto done;
     if ((st = dalloc(&wadj, nadj + 1, s)) != DSD_OK) goto done;
     if ((st = dalloc(&ctrl, 1, s)) != DSD_OK) goto done;
+    if (tsh_g.cs &&
+        (st = dalloc(&rows_g, (size_t)tsh_g.cap * (tsh_g.cap / 32), s)) != DSD_OK)
+        goto done;
     if (h >= 5) {
         P.big_cap = g->m * 2 + 1;
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
@@ -1211,6 +1348,41 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
         else if (NT == 512) e = launch_peel<512>(P, sms, smem, s, &grid);
         else e = launch_peel<256>(P, sms, smem, s, &grid);
     }
+    if (e == cudaSuccess && P.tail_max) {
+        // the launches run only if something was handed over (they read tail_n)
+        TailParams T;
+        memset(&T, 0, sizeof(T));
+        T.h = h;
+        T.off = off;
+        T.wend = P.wend;
+        T.wadj = P.wadj;
+        T.sl = P.sl;
+        T.deg = P.deg;
+        T.list[0] = P.alive[0];
+        T.list[1] = P.alive[1];
+        T.core = P.core;
+        T.rnd = P.rnd;
+        T.lvl_k = P.lvl_k;
+        T.lvl_size = P.lvl_size;
+        T.lvl_mu = P.lvl_mu;
+        T.ctrl = ctrl;
+        if (tsh_g.cs) {
+            T.cap = tsh_g.cap;
+            T.rows_cap = tsh_g.cap / tsh_g.cs;
+            T.W = tsh_g.cap / 32;
+            T.pass_below = tsh_d.cap;
+            T.rows_g = rows_g;
+            e = launch_tail<true>(T, tsh_g, s);
+        }
+        if (e == cudaSuccess) {
+            T.cap = tsh_d.cap;
+            T.rows_cap = tsh_d.cap / tsh_d.cs;
+            T.W = tsh_d.cap / 32;
+            T.pass_below = 0;
+            T.rows_g = nullptr;
+            e = launch_tail<false>(T, tsh_d, s);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(PeelCtrl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -1239,6 +1411,10 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     res->threads = NT;
     res->grid = grid;
     res->small_round = hc.small_round;
+    res->tail_n = hc.tail_entry;
+    res->tail_round = hc.tail_entry_round;
+    res->tail_ns = hc.tail_ns;
+    for (int i = 0; i < 5; i++) res->tail_tph[i] = hc.tail_tph[i];
     for (int i = 0; i < 8; i++) res->tph[i] = hc.tph[i];
 done:
     dev_free(sl, s);
@@ -1246,6 +1422,7 @@ done:
     dev_free(wmeta, s);
     dev_free(wadj, s);
     dev_free(ctrl, s);
+    dev_free(rows_g, s);
     dev_free(big, s);
     dev_free(jblk, s);
     return st;

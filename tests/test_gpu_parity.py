@@ -173,6 +173,34 @@ def test_peel_regimes(L, orc, limit):
         L.dsd_set_peel_small_limit(16384)
 
 
+@pytest.mark.parametrize("tail", [0, 64, 1000, 8000, 1 << 30])
+def test_peel_tail_limits(L, orc, tail):
+    """The cluster tail kernel (h = 2, 3: the alive subgraph as bitmap rows in
+    distributed shared memory) finishes the levels exactly as the persistent
+    kernel does, whatever the hand-over size."""
+    L.dsd_set_peel_tail_limit(tail)
+    try:
+        n, s, d, _ = gg.workload("cl50k")
+        compare_all(L, orc, n, s, d, (2, 3), csr=False)
+        with L.Graph.from_edges(n, s, d) as g:
+            g.core_app(3)
+            st = L.dsd_peel_stats(g.handle, 1)
+            if tail == 0:
+                assert st["tail_n"] == 0
+            elif tail >= 1000:
+                assert 0 < st["tail_n"] <= tail
+        for i in range(4):
+            n, s, d = gg.random_small(400, 0.06, seed=950 + i)
+            compare_all(L, orc, n, s, d, (2, 3, 4), csr=False)
+        # a dense block peeled entirely inside the tail, and an empty one
+        n, s, d = gg.er(600, 0.3, seed=5)
+        compare_all(L, orc, n, s, d, (2, 3), csr=False)
+        compare_all(L, orc, 50, np.zeros(0, np.uint32), np.zeros(0, np.uint32), (2, 3),
+                    csr=False)
+    finally:
+        L.dsd_set_peel_tail_limit(1 << 30)
+
+
 def test_er2000_bruteforce_subsamples(L, orc):
     """Configuration 1: 16-vertex induced subsamples against brute force."""
     import bruteforce as bf
