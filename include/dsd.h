@@ -336,9 +336,10 @@ dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* l
  * mark/bitmaps, clique enumeration; then the alive vertices handed to the
  * cluster tail kernel (0 if none), the round of the hand-over, the tail
  * kernel's time (ns) and its lead CTA's time (ns) in: building the rows,
- * frontier broadcast, level jumps and frontier lists, clique enumeration,
- * retiring.  Zeros if that peel has not run. */
-#define DSD_PEEL_STATS 27
+ * frontier broadcast, level jumps and frontier lists, candidate numbering,
+ * candidate work, the barrier after it, retiring.  Zeros if that peel has
+ * not run. */
+#define DSD_PEEL_STATS 29
 dsd_status dsd_peel_stats(dsd_graph* g, int which, uint64_t* out);
 
 #ifdef __cplusplus

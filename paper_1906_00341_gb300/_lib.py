@@ -105,7 +105,8 @@ PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "c
               "t_large_retire", "t_large_scan", "t_large_jump", "t_large_enum",
               "t_small_retire", "t_small_jump", "t_small_mark", "t_small_enum",
               "tail_n", "tail_round", "tail_ns",
-              "t_tail_build", "t_tail_front", "t_tail_jump", "t_tail_enum", "t_tail_retire")
+              "t_tail_build", "t_tail_front", "t_tail_jump", "t_tail_prefix", "t_tail_work",
+              "t_tail_sync", "t_tail_retire")
 
 
 def load(path: str = LIB_PATH):

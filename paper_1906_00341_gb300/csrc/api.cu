@@ -38,7 +38,7 @@ void record_peel(dsd_graph* g, int which, const PeelResult& r) {
     o[19] = r.tail_n;
     o[20] = r.tail_round;
     o[21] = r.tail_ns;
-    for (int i = 0; i < 5; i++) o[22 + i] = r.tail_tph[i];
+    for (int i = 0; i < 7; i++) o[22 + i] = r.tail_tph[i];
 }
 
 void prof_begin(dsd_graph* g, int phase) {

@@ -92,7 +92,7 @@ struct PeelResult {
     uint32_t tail_n = 0;      // alive vertices handed to the cluster tail kernel
     uint32_t tail_round = 0;  // round of the hand-over
     uint64_t tail_ns = 0;     // the tail kernel's duration
-    uint64_t tail_tph[5] = {};  // the tail's time per phase (ns)
+    uint64_t tail_tph[7] = {};  // the tail's time per phase (ns)
 };
 // off/adj/split: CSR in the working id space (split may be null for h = 2).
 // deg: [n] clique-degrees in, destroyed on return.  core/rnd: [n] outputs

@@ -95,7 +95,7 @@ struct PeelCtrl {
     uint32_t pad4;
     unsigned long long mu_tail;     // mu of the alive graph at the hand-over
     unsigned long long tail_ns;     // the tail kernel's duration
-    unsigned long long tail_tph[5]; // tail CTA 0's time: build, A+sync, jump+list, C+sync, D
+    unsigned long long tail_tph[7]; // tail lead CTA: build, A+sync, jump+list, C prefix, C work, C sync, D
 };
 
 // Byte meter.  Every global-memory element the algorithm reads or writes is
@@ -1414,7 +1414,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     res->tail_n = hc.tail_entry;
     res->tail_round = hc.tail_entry_round;
     res->tail_ns = hc.tail_ns;
-    for (int i = 0; i < 5; i++) res->tail_tph[i] = hc.tail_tph[i];
+    for (int i = 0; i < 7; i++) res->tail_tph[i] = hc.tail_tph[i];
     for (int i = 0; i < 8; i++) res->tph[i] = hc.tph[i];
 done:
     dev_free(sl, s);
