@@ -25,7 +25,7 @@
 //       when the alive set has halved, drop removed vertices     |
 //       from the rows of alive vertices                          | barrier
 //   P2  enumerate the cliques each v in F_r destroys; decrement   | barrier
-//   P2b (h >= 5) candidate sets above 32 vertices, one block each | barrier
+//   P2b (h >= 4) candidate sets above 32 vertices, one block each | barrier
 //
 // Small regime (the long tail of tiny levels: at most `asmall` vertices
 // alive).  Every block holds a slice of the alive list and the whole
@@ -396,7 +396,7 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         }
     } else {
         if (nc < (uint32_t)r) return;
-        if (r >= 3 && nc > 32) {
+        if (nc > 32 && (r >= 3 || P.big_cap)) {
             if (lane == 0) {
                 uint32_t at = atomicAdd(big_cnt, 1u);
                 if (at < P.big_cap) P.big[at] = make_uint2(v, w);
@@ -453,7 +453,8 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
     }
 }
 
-// A (v, w) item whose candidate set exceeds 32 vertices (h >= 5): one block.
+// A (v, w) item whose candidate set exceeds 32 vertices (h >= 4): one block,
+// bitmap rows of G[C] and a warp-level DFS per starting candidate.
 __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                             uint32_t* next, uint32_t* next_cnt, uint32_t* smem,
                             unsigned long long& destroyed, unsigned long long& bytes) {
@@ -840,7 +841,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
                 BARRIER(3);
                 // ------------------------------------------------- P2b
-                if (P.h >= 5) {
+                if (P.big_cap) {
                     uint32_t nb = c->big_cnt[r % 3];
                     if (nb) {
                         if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
@@ -1053,7 +1054,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             unsigned long long bd = block_sum<NT>(destroyed, s_red);
             if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
             BARRIER(7);
-            if (P.h >= 5) {
+            if (P.big_cap) {
                 uint32_t nb = c->big_cnt[r % 3];
                 if (nb) {
                     if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
@@ -1255,8 +1256,11 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
                   "(max here %u)", h, kBitmapMax, maxdplus);
         return DSD_ERR_UNSUPPORTED;
     }
+    // Big items (candidate sets above 32 vertices, one block each) for
+    // h >= 5, and for h = 4 when every candidate set fits 32-word rows.
+    const bool big_items = h >= 5 || (h == 4 && maxdplus <= kBitmapMax);
     // Shared memory: per-warp candidate buffers (h >= 3) or the big-item
-    // bitmap (h >= 5), then the small-regime alive list, frontier and
+    // bitmap, then the small-regime alive list, frontier and
     // neighbourhood bitmaps.  Block size: the largest whose candidate
     // buffers leave room for the small-regime lists.
     const size_t budget = 220 * 1024;
@@ -1265,7 +1269,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     if (h >= 3)
         while (NT > 256 && (size_t)(NT / 32) * warp_words * 4 > budget / 2) NT >>= 1;
     size_t work = h >= 3 ? (size_t)(NT / 32) * warp_words : 0;
-    if (h >= 5) {
+    if (big_items) {
         size_t W = (P.cap + 31) / 32;
         size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
         if (big > work) work = big;
@@ -1318,7 +1322,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     if (tsh_g.cs &&
         (st = dalloc(&rows_g, (size_t)tsh_g.cap * (tsh_g.cap / 32), s)) != DSD_OK)
         goto done;
-    if (h >= 5) {
+    if (big_items) {
         P.big_cap = g->m * 2 + 1;
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
     }
