@@ -53,6 +53,8 @@ def _load():
     lib.orc_clique_degrees.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u64p, _u64p]
     lib.orc_vertex_clique_degree.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
                                              ctypes.c_uint32, _u64p]
+    lib.orc_vertex_clique_degrees.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
+                                              _u32p, ctypes.c_uint32, _u64p]
     lib.orc_induced_clique_count.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
                                              _u8p, _u64p]
     lib.orc_core_decompose.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
@@ -61,7 +63,8 @@ def _load():
                                         ctypes.c_uint64, _u8p]
     lib.orc_level_stats.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u64p,
                                     _u64p, ctypes.c_uint32, _u64p, _u64p]
-    for f in ("orc_clique_degrees", "orc_vertex_clique_degree", "orc_induced_clique_count",
+    for f in ("orc_clique_degrees", "orc_vertex_clique_degree", "orc_vertex_clique_degrees",
+              "orc_induced_clique_count",
               "orc_core_decompose", "orc_threshold_prune", "orc_level_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -123,6 +126,16 @@ def vertex_clique_degree(g: Graph, h: int, v: int) -> int:
     _check(lib.orc_vertex_clique_degree(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), h, v,
                                         _p(out, _u64p)))
     return int(out[0])
+
+
+def vertex_clique_degrees(g: Graph, h: int, vs) -> np.ndarray:
+    """Def. 3 for each vertex of vs (one listing order for all)."""
+    lib = _load()
+    vs = np.ascontiguousarray(vs, np.uint32)
+    out = np.zeros(max(vs.size, 1), np.uint64)
+    _check(lib.orc_vertex_clique_degrees(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), h,
+                                         _p(vs, _u32p), vs.size, _p(out, _u64p)))
+    return out[: vs.size]
 
 
 def induced_clique_count(g: Graph, h: int, mask) -> int:

@@ -14,7 +14,8 @@
  *   orc_build_csr            Sec. 2 "Data model": undirected, simple graph.
  *   orc_clique_degrees       Def. 2 (clique instance), Def. 3 (clique-degree),
  *                            Def. 4 (mu = number of instances).
- *   orc_vertex_clique_degree Def. 3 for one vertex.
+ *   orc_vertex_clique_degree Def. 3 for one vertex (orc_vertex_clique_degrees:
+ *                            for many, sharing one listing order).
  *   orc_core_decompose       Algorithm 3 ((k,Psi)-core decomposition), in the
  *                            paper's steps: take a minimum clique-degree
  *                            vertex v, record core[v] = deg[v], and for each
@@ -354,6 +355,28 @@ int orc_vertex_clique_degree(uint32_t n, const uint64_t* off, const uint32_t* ad
     if (!L.deg) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
     list_containing(&L, g.new_of[v], NULL);
     *out = L.mu;
+    free(L.deg); lister_free(&L); wg_free(&g);
+    return ORC_OK;
+}
+
+/* Def. 3 for each of count vertices vs[i] into out[i], with the listing
+ * order built once (the same listing as orc_vertex_clique_degree). */
+int orc_vertex_clique_degrees(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                              int h, const uint32_t* vs, uint32_t count, uint64_t* out) {
+    if (check_h(h)) return ORC_EINVAL;
+    for (uint32_t i = 0; i < count; i++)
+        if (vs[i] >= n) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    if (lister_init(&L, &g, h, visit_count)) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    L.deg = (uint64_t*)calloc((size_t)n, sizeof(uint64_t));
+    if (!L.deg) { lister_free(&L); wg_free(&g); return ORC_ENOMEM; }
+    for (uint32_t i = 0; i < count; i++) {
+        L.mu = 0;
+        list_containing(&L, g.new_of[vs[i]], NULL);
+        out[i] = L.mu;
+    }
     free(L.deg); lister_free(&L); wg_free(&g);
     return ORC_OK;
 }

@@ -1,0 +1,122 @@
+"""Parity at the full benchmark sizes, in the launch configuration the
+benchmark times (edge list resident on the device, dsd_graph_from_edges +
+dsd_core_app with device outputs).
+
+* Chung-Lu n = 1,000,000 (10M draws, exponent 2.1, planted G(200, 0.5)),
+  h = 3: every output against the oracle, element by element.
+* R-MAT scale 22, h = 4: the oracle cannot list its 1.2e11 4-cliques in
+  test time, so the checks are sampled or structural -- the clique-degrees
+  of sampled vertices against the oracle's per-vertex count, sum(deg) =
+  h mu, core <= deg, the level records' monotonicity, and the k_max core
+  and densest level recomputed from their induced subgraphs.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1906_00341_gb300 import graphgen as gg
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1906_00341_gb300 import build as b
+    b.build()
+    from paper_1906_00341_gb300 import _lib
+    _lib.load()
+    return _lib
+
+
+def _device_graph(L, n, s, d):
+    import torch
+    src = torch.from_numpy(s.astype(np.int32)).cuda()
+    dst = torch.from_numpy(d.astype(np.int32)).cuda()
+    return L.Graph.from_edges(n, src, dst), (src, dst)
+
+
+def test_cl1m_h3_full_parity(L, orc):
+    n, s, d, _ = gg.workload("cl1m")
+    og = orc.csr(n, s, d)
+    g, keep = _device_graph(L, n, s, d)
+    with g:
+        assert g.m == og.m
+        r = g.core_app(3, mem="device")
+        kc = r["kmax_core"].cpu().numpy().astype(np.uint32)
+        de = r["densest"].cpu().numpy().astype(np.uint32)
+        deg, mu = g.clique_degrees(3)
+        core, kmax = g.core_decompose(3)
+        lk, ls, lm = g.level_stats(3)
+    wdeg, wmu = orc.clique_degrees(og, 3)
+    assert mu == wmu and np.array_equal(deg, wdeg)
+    wcore, wk = orc.core_decompose(og, 3)
+    assert kmax == wk and np.array_equal(core, wcore)
+    wk_, ws_, wm_ = orc.level_stats(og, 3, wcore)
+    assert np.array_equal(lk, wk_) and np.array_equal(ls, ws_) and np.array_equal(lm, wm_)
+    w = orc.core_app(og, 3, wcore, wk)
+    assert r["kmax"] == w["kmax"] and np.array_equal(kc, w["kmax_core"])
+    assert r["kmax_core_mu"] == w["kmax_core_mu"]
+    assert r["best_k"] == w["best_k"] and np.array_equal(de, w["densest"])
+    assert (r["densest_mu"], r["densest_size"]) == (w["densest_mu"], w["densest_size"])
+
+
+def _induced(s, d, keep_mask):
+    sel = keep_mask[s] & keep_mask[d]
+    newid = np.cumsum(keep_mask) - 1
+    return int(keep_mask.sum()), newid[s[sel]].astype(np.uint32), newid[d[sel]].astype(np.uint32)
+
+
+def test_rmat22_h4_sampled_and_structural(L, orc):
+    h = 4
+    n, s, d, _ = gg.workload("rmat22")
+    og = orc.csr(n, s, d)
+    g, keep = _device_graph(L, n, s, d)
+    with g:
+        assert g.m == og.m
+        deg, mu = g.clique_degrees(h)
+        core, kmax = g.core_decompose(h)
+        lk, ls, lm = g.level_stats(h)
+        r = g.core_app(h)
+    # sampled clique-degrees against the oracle's per-vertex count
+    dg = np.diff(og.off.astype(np.int64))
+    rng = np.random.default_rng(22)
+    low = np.flatnonzero((dg >= 3) & (dg <= 48))
+    mid = np.flatnonzero((dg > 48) & (dg <= 160))
+    picks = np.concatenate([rng.choice(low, 150, replace=False), rng.choice(mid, 30, replace=False)])
+    want = orc.vertex_clique_degrees(og, h, picks)
+    assert np.array_equal(deg[picks], want)
+    # sum of clique-degrees = h mu, core <= deg, k_max = max core
+    assert int(deg.astype(object).sum()) == h * mu
+    assert np.all(core <= deg)
+    assert kmax == int(core.max()) == r["kmax"]
+    # level records: k strictly increasing, |R_k| and mu(R_k) decreasing
+    assert lk[0] >= 0 and np.all(np.diff(lk.astype(np.int64)) > 0)
+    assert np.all(np.diff(ls.astype(np.int64)) < 0) and ls[0] == n
+    assert np.all(np.diff(lm.astype(object)) <= 0) and int(lm[0]) == mu
+    assert r["best_k"] in set(lk.tolist())
+    j = int(np.flatnonzero(lk == r["best_k"])[0])
+    assert (r["densest_mu"], r["densest_size"]) == (int(lm[j]), int(ls[j]))
+    # the k_max core and the densest level, rebuilt as graphs of their own:
+    # every vertex of the k_max core has >= k_max h-cliques inside it, and
+    # the densest level's h-clique count is the reported numerator
+    for verts, k_need, mu_want in ((r["kmax_core"], kmax, r["kmax_core_mu"]),
+                                   (r["densest"], r["best_k"], r["densest_mu"])):
+        mask = np.zeros(n, bool)
+        mask[verts] = True
+        assert np.array_equal(np.flatnonzero(core >= k_need), np.sort(verts))
+        nn, ss, dd = _induced(og_src(og), og_dst(og), mask)
+        with L.Graph.from_edges(nn, ss, dd) as sub:
+            sdeg, smu = sub.clique_degrees(h)
+        assert smu == mu_want
+        assert int(sdeg.min()) >= k_need
+
+
+def og_src(og):
+    return np.repeat(np.arange(og.n, dtype=np.uint32), np.diff(og.off.astype(np.int64)))
+
+
+def og_dst(og):
+    return og.adj.astype(np.uint32)

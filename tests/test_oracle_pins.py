@@ -341,3 +341,18 @@ def test_densest_level_is_argmax(orc):
                 best = (rho, k, mask)
         assert Fraction(r["densest_mu"], r["densest_size"]) == best[0]
         assert r["densest"].tolist() == np.nonzero(best[2])[0].tolist()
+
+
+def test_vertex_clique_degrees_batch_matches_single(orc):
+    # the batched per-vertex count shares one listing order; it must agree
+    # with the single-vertex call and with the full clique-degree vector
+    import numpy as np
+    from paper_1906_00341_gb300 import graphgen as gg
+    n, s, d = gg.random_small(120, 0.15, seed=11)
+    g = orc.csr(n, s, d)
+    for h in (2, 3, 4):
+        full, _ = orc.clique_degrees(g, h)
+        vs = np.array([0, 5, 17, 17, 119, 64], np.uint32)
+        got = orc.vertex_clique_degrees(g, h, vs)
+        assert np.array_equal(got, full[vs])
+        assert [orc.vertex_clique_degree(g, h, int(v)) for v in vs] == got.tolist()
