@@ -16,7 +16,8 @@ more objects on the same line (rank 0, skipped with --no-learned /
   learned -- the trained density proposal: dsd_core_app_seeded vs
              dsd_core_app on the held-out Chung-Lu graph n = 4,000,000 (64M
              draws, exponent 2.2, five planted G(300, 0.4)), h = 3: speedup,
-             acceptance rate, identical outputs;
+             acceptance rate, identical outputs; beside it CoreApp's own
+             top-down schedule (dsd_core_app_topdown) on the same graph;
   batched -- 4096 mixed graphs (h in {2,3,4}) in one CUDA-graph replay of the
              persistent batch kernel vs a host loop of the plain path.
 
@@ -321,6 +322,8 @@ def run_learned(args, local):
         if model is None:
             r = L.dsd_core_app(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
             info = None
+        elif model == "topdown":
+            r, info = L.dsd_core_app_topdown(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
         else:
             r, info = L.dsd_core_app_seeded(g, h, model.handle, kc.data_ptr(), de.data_ptr(),
                                             L.DSD_MEM_DEVICE)
@@ -334,7 +337,8 @@ def run_learned(args, local):
 
     out = {}
     ref = None
-    for name, model in (("plain", None), ("seeded", M), ("untrained", untrained)):
+    for name, model in (("plain", None), ("seeded", M), ("untrained", untrained),
+                        ("topdown", "topdown")):
         for _ in range(args.warmup):
             g, r, info = call(model)
             L.dsd_graph_destroy(g)
@@ -352,11 +356,14 @@ def run_learned(args, local):
             if ref is None:
                 ref = a
             same = same and a == ref
-            if info is not None:
+            if info is not None and model != "topdown":
                 acc.append(int(info.accepted))
             L.dsd_graph_destroy(g)
         rec = {"ms": float(np.mean(times)), "identical": bool(same)}
-        if info is not None:
+        if model == "topdown":
+            rec.update(passes=int(info.passes), x=int(info.x), gamma_out=int(info.gamma_out),
+                       sub_n=int(info.sub_n), sub_m=int(info.sub_m))
+        elif info is not None:
             rec.update(accepted=float(np.mean(acc)), rho_prime=float(info.rho_prime),
                        seed_k=int(info.seed_k), x0=int(info.x0), sub_n=int(info.sub_n),
                        sub_m=int(info.sub_m))
@@ -368,9 +375,12 @@ def run_learned(args, local):
         "train_graphs": M.header.get("meta", {}).get("graphs"),
         "speedup": out["plain"]["ms"] / out["seeded"]["ms"],
         "acceptance_rate": out["seeded"]["accepted"],
-        "identical_output": out["seeded"]["identical"] and out["untrained"]["identical"],
+        "identical_output": (out["seeded"]["identical"] and out["untrained"]["identical"]
+                             and out["topdown"]["identical"]),
+        "topdown_speedup": out["plain"]["ms"] / out["topdown"]["ms"],
         "densest": [int(ref[4]), int(ref[5])], "kmax": int(ref[0]),
         "plain": out["plain"], "seeded": out["seeded"], "untrained": out["untrained"],
+        "topdown": out["topdown"],
         "timing": "CUDA events per call (CSR build + decomposition), mean of %d after %d "
                   "warm-up, L2 flushed between calls" % (args.steps, args.warmup),
     }

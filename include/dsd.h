@@ -85,9 +85,10 @@ dsd_status dsd_set_wait_limit_ms(uint32_t ms);
  * depend on it.  Process-wide; applies to calls started afterwards. */
 dsd_status dsd_set_peel_small_limit(uint32_t max_alive);
 /* Largest alive set whose remaining levels (h = 2, 3) are finished by one
- * thread-block cluster holding the alive subgraph as bitmap rows in
- * distributed shared memory (default: as large as the cluster holds, about
- * 4,600 vertices; 0 = never).  Results do not depend on it.  Process-wide. */
+ * thread-block cluster holding the alive subgraph as bitmap rows (in global
+ * memory up to 16,384 vertices for h = 3, in the cluster's distributed shared
+ * memory below about 4,600; the default is as large as those hold; 0 =
+ * never).  Results do not depend on it.  Process-wide. */
 dsd_status dsd_set_peel_tail_limit(uint32_t max_alive);
 
 /* ---------------------------------------------------------------- graphs */
@@ -252,6 +253,27 @@ typedef struct {
 dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* m, uint32_t* kmax_core,
                                uint32_t* densest, int mem, dsd_core_app_result* r,
                                dsd_seed_info* info);
+
+/* ---------------------------------------------- CoreApp's top-down schedule */
+
+typedef struct {
+    uint32_t passes;          /* windows decomposed */
+    uint32_t sub_n;           /* vertices of the last window */
+    uint64_t x;               /* its edge-core order: the window is {core_2 >= x} */
+    uint64_t gamma_out;       /* the largest C(core_2, h-1) outside it */
+    uint64_t sub_m;           /* its edges */
+} dsd_topdown_info;
+
+/* dsd_core_app through CoreApp's own schedule (Algorithm 6, Sec. 5.2):
+ * windows of the vertices with the largest bound gamma(v) = C(core_2(v), h-1)
+ * (edge cores, at least 1024 vertices, doubling), each peeled from level
+ * K = gamma_out + 1 (gamma_out: the largest gamma outside the window; one
+ * cascade prunes to R_K), until the window's k_max is >= K and its densest
+ * level at or above K has density >= K - 1 (then no level below K is
+ * denser).  Outputs identical to dsd_core_app; r->nlevels counts
+ * the levels at or above K.  info (may be NULL) describes the schedule. */
+dsd_status dsd_core_app_topdown(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
+                                int mem, dsd_core_app_result* r, dsd_topdown_info* info);
 
 /* ------------------------------------------------------------- batches */
 

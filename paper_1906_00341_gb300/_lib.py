@@ -41,6 +41,11 @@ class CoreAppResult(ctypes.Structure):
                 ("nlevels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class TopdownInfo(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_uint32), ("sub_n", ctypes.c_uint32), ("x", ctypes.c_uint64),
+                ("gamma_out", ctypes.c_uint64), ("sub_m", ctypes.c_uint64)]
+
+
 class SeedInfo(ctypes.Structure):
     _fields_ = [("rho_prime", ctypes.c_float), ("accepted", ctypes.c_uint32),
                 ("seed_k", ctypes.c_uint64), ("x0", ctypes.c_uint64),
@@ -98,6 +103,8 @@ SIGNATURES = {
     "dsd_graph_features": (_int, [_P, _int, _P, _int]),
     "dsd_core_app_seeded": (_int, [_P, _int, _P, _P, _P, _int, ctypes.POINTER(CoreAppResult),
                                    ctypes.POINTER(SeedInfo)]),
+    "dsd_core_app_topdown": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult),
+                                    ctypes.POINTER(TopdownInfo)]),
 }
 
 PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
@@ -375,6 +382,14 @@ def dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem):
     return r, info
 
 
+def dsd_core_app_topdown(g, h, kcore_ptr, densest_ptr, mem):
+    r = CoreAppResult()
+    info = TopdownInfo()
+    _check(load().dsd_core_app_topdown(g, h, kcore_ptr, densest_ptr, mem, ctypes.byref(r),
+                                       ctypes.byref(info)))
+    return r, info
+
+
 class Model:
     """Owns one dsd_model handle (the density-proposal network).  Inputs and
     outputs are float32 numpy arrays; the arithmetic runs in libdsd."""
@@ -600,6 +615,21 @@ class Graph:
         out["seed"] = dict(rho_prime=float(info.rho_prime), accepted=int(info.accepted),
                            seed_k=int(info.seed_k), x0=int(info.x0), sub_n=int(info.sub_n),
                            sub_m=int(info.sub_m))
+        return out
+
+    def core_app_topdown(self, h, mem="host", sets=True):
+        kc = self._alloc(self.n, 4, mem) if sets else None
+        de = self._alloc(self.n, 4, mem) if sets else None
+        r, info = dsd_core_app_topdown(self.handle, h, self._ptr(kc) if sets else 0,
+                                       self._ptr(de) if sets else 0, self._memc(mem))
+        out = dict(kmax=int(r.kmax), kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                   densest_mu=int(r.densest_mu), densest_size=int(r.densest_size),
+                   kmax_core_size=int(r.kmax_core_size), nlevels=int(r.nlevels))
+        if sets:
+            out["kmax_core"] = kc[: r.kmax_core_size]
+            out["densest"] = de[: r.densest_size]
+        out["schedule"] = dict(passes=int(info.passes), sub_n=int(info.sub_n), x=int(info.x),
+                               gamma_out=int(info.gamma_out), sub_m=int(info.sub_m))
         return out
 
     def set_profiling(self, on=True):

@@ -107,6 +107,27 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
 // level record is then (kstart - 1, |V|, mu) and the core numbers it assigns
 // are not core numbers.  Levels at or above kstart are exact.
 
+// The edge core {core_2 >= x0} of g as a graph of its own (ids ascend with
+// g's ids), its h-clique counts, and its peel from level kstart (levels at or
+// above kstart exact).  Used by the seeded and the top-down CoreApp calls.
+struct SubCore {
+    dsd_graph* H = nullptr;
+    uint32_t* orig = nullptr;     // H id -> g id
+    uint64_t* core = nullptr;     // H rank space
+    uint64_t* lk = nullptr;       // level records [nlevels]
+    uint32_t* ls = nullptr;
+    uint64_t* lm = nullptr;
+    uint64_t nh = 0, mh = 0;
+    unsigned long long mu = 0;
+    PeelResult pr;
+};
+dsd_status sub_core_build(dsd_graph* g, int h, uint64_t x0, uint64_t kstart, SubCore* S);
+// The g ids (ascending) of the H vertices with core >= thr into out (size
+// entries; host or device memory by mem).
+dsd_status sub_core_emit(dsd_graph* g, const SubCore& S, uint64_t thr, uint32_t size,
+                         uint32_t* out, int mem);
+void sub_core_free(SubCore* S, cudaStream_t s);
+
 // Statistics of the last peel runs: [0] degeneracy peel, [1] (k,Psi) peel.
 void record_peel(dsd_graph* g, int which, const PeelResult& r);
 

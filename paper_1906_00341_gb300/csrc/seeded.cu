@@ -153,8 +153,7 @@ __global__ void k_seed_select(uint32_t nl, const uint64_t* lk, const uint32_t* l
 
 // core of H vertex (H ids) from its rank-space core; flags >= threshold.
 __global__ void k_sub_flags_core(uint32_t nh, const uint32_t* old_of_rank, const uint64_t* core_rank,
-                                 const unsigned long long* thr, uint32_t* flag_h) {
-    unsigned long long t = *thr;
+                                 unsigned long long t, uint32_t* flag_h) {
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nh;
          p += (uint64_t)gridDim.x * blockDim.x)
         flag_h[old_of_rank[p]] = core_rank[p] >= t ? 1u : 0u;
@@ -196,6 +195,121 @@ uint64_t min_x_for(uint64_t k, int h, uint64_t cap) {
 }
 
 }  // namespace
+
+void sub_core_free(SubCore* S, cudaStream_t s) {
+    if (S->H) dsd_graph_destroy(S->H);
+    void* ptrs[] = {S->orig, S->core, S->lk, S->ls, S->lm};
+    for (void* p : ptrs) dev_free(p, s);
+    *S = SubCore();
+}
+
+dsd_status sub_core_build(dsd_graph* g, int h, uint64_t x0, uint64_t kstart, SubCore* S) {
+    *S = SubCore();
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    uint32_t *flag = nullptr, *map = nullptr, *cnt = nullptr, *es = nullptr;
+    uint64_t *pos = nullptr, *epos = nullptr;
+    unsigned long long* deg = nullptr;
+    dsd_status st = DSD_OK;
+    cudaError_t e = cudaSuccess;
+#define SSTEP(x)                         \
+    do {                                 \
+        st = (x);                        \
+        if (st != DSD_OK) goto done;     \
+    } while (0)
+#define SCU(x)                                                                          \
+    do {                                                                                \
+        e = (x);                                                                        \
+        if (e != cudaSuccess) { st = cuda_fail(e, #x, __FILE__, __LINE__); goto done; } \
+    } while (0)
+    SSTEP(dalloc(&flag, (size_t)n + 1, s));
+    SSTEP(dalloc(&map, (size_t)n + 1, s));
+    SSTEP(dalloc(&cnt, (size_t)n + 1, s));
+    SSTEP(dalloc(&pos, (size_t)n + 1, s));
+    SSTEP(dalloc(&epos, (size_t)n + 1, s));
+    if (n) {
+        k_sub_flags<<<grid_n(n), 256, 0, s>>>(n, g->core2, x0, flag);
+        note_launch();
+    }
+    SSTEP(exclusive_scan_u32_to_u64(flag, pos, n, s));
+    SCU(cudaMemcpyAsync(&S->nh, pos + n, 8, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    SSTEP(dalloc(&S->orig, S->nh + 1, s));
+    if (n) {
+        k_sub_map<<<grid_n(n), 256, 0, s>>>(n, flag, pos, map, S->orig);
+        k_sub_count<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, cnt);
+        note_launch();
+        note_launch();
+    }
+    SSTEP(exclusive_scan_u32_to_u64(cnt, epos, n, s));
+    SCU(cudaMemcpyAsync(&S->mh, epos + n, 8, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    SSTEP(dalloc(&es, 2 * S->mh + 2, s));
+    if (n) {
+        k_sub_fill<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, epos, es,
+                                                           es + S->mh);
+        note_launch();
+    }
+    SCU(cudaGetLastError());
+    S->H = new (std::nothrow) dsd_graph();
+    if (!S->H) {
+        st = DSD_ERR_NOMEM;
+        goto done;
+    }
+    S->H->stream = s;
+    S->H->n = (uint32_t)S->nh;
+    S->H->device = g->device;
+    SSTEP(build_csr(S->H, S->mh, es, es + S->mh));
+    SSTEP(ensure_order(S->H));
+    SSTEP(dalloc(&deg, S->nh + 2, s));
+    SSTEP(dalloc(&S->core, S->nh + 1, s));
+    SSTEP(dalloc(&S->lk, S->nh + 1, s));
+    SSTEP(dalloc(&S->lm, S->nh + 1, s));
+    SSTEP(dalloc(&S->ls, S->nh + 1, s));
+    SSTEP(count_cliques(S->H, h, deg, deg + S->nh + 1));
+    SCU(cudaMemcpyAsync(&S->mu, deg + S->nh + 1, 8, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    SSTEP(run_peel(S->H, h, S->H->n, S->H->roff, S->H->radj, S->H->rsplit, S->H->maxdplus, deg,
+                   S->mu, S->core, nullptr, S->lk, S->ls, S->lm, &S->pr, kstart));
+done:
+#undef SSTEP
+#undef SCU
+    void* ptrs[] = {flag, map, cnt, es, pos, epos, deg};
+    for (void* p : ptrs) dev_free(p, s);
+    if (st != DSD_OK) sub_core_free(S, s);
+    return st;
+}
+
+dsd_status sub_core_emit(dsd_graph* g, const SubCore& S, uint64_t thr, uint32_t size,
+                         uint32_t* out, int mem) {
+    if (!out || S.nh == 0) return DSD_OK;
+    cudaStream_t s = g->stream;
+    uint32_t* fh = nullptr;
+    uint64_t* ph = nullptr;
+    uint32_t* tmp = nullptr;
+    dsd_status st = dalloc(&fh, S.nh + 1, s);
+    if (st == DSD_OK) st = dalloc(&ph, S.nh + 1, s);
+    if (st == DSD_OK && mem == DSD_MEM_HOST) st = dalloc(&tmp, S.nh + 1, s);
+    if (st == DSD_OK) {
+        k_sub_flags_core<<<grid_n(S.nh), 256, 0, s>>>((uint32_t)S.nh, S.H->old_of, S.core, thr, fh);
+        note_launch();
+        st = exclusive_scan_u32_to_u64(fh, ph, S.nh, s);
+    }
+    if (st == DSD_OK) {
+        k_sub_emit<<<grid_n(S.nh), 256, 0, s>>>((uint32_t)S.nh, fh, ph, S.orig, tmp ? tmp : out);
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && tmp)
+            e = cudaMemcpyAsync(out, tmp, (size_t)size * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "core set", __FILE__, __LINE__);
+    }
+    dev_free(fh, s);
+    dev_free(ph, s);
+    dev_free(tmp, s);
+    return st;
+}
+
 }  // namespace dsd
 
 using namespace dsd;
@@ -241,118 +355,34 @@ dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* M, uint32_t* kmax
         if (x0 > g->degeneracy) try_seed = false;   // no vertex can reach level k
     }
     if (try_seed) {
-        dsd_graph* H = nullptr;
-        uint32_t *flag = nullptr, *map = nullptr, *orig = nullptr, *cnt = nullptr, *es = nullptr;
-        uint64_t *pos = nullptr, *epos = nullptr;
-        unsigned long long* deg = nullptr;
-        uint64_t* core = nullptr;
-        uint64_t *lk = nullptr, *lm = nullptr;
-        uint32_t* ls = nullptr;
-        SeedRes* sr = nullptr;
-        SeedRes hs;
-        memset(&hs, 0, sizeof(hs));
-        uint64_t nh = 0, mh = 0;
-        unsigned long long muh = 0;
-        PeelResult pr;
-        cudaError_t e = cudaSuccess;
         int Eexp = 0;
         float mant = frexpf(rho, &Eexp);            // rho = mant * 2^Eexp, mant in [0.5, 1)
         unsigned long long Mn = (unsigned long long)ldexpf(mant, 24);
         int E = Eexp - 24;
-#define SSTEP(x)                                         \
-    do {                                                 \
-        st = (x);                                        \
-        if (st != DSD_OK) goto seed_done;                \
-    } while (0)
-#define SCU(x)                                                                      \
-    do {                                                                            \
-        e = (x);                                                                    \
-        if (e != cudaSuccess) { st = cuda_fail(e, #x, __FILE__, __LINE__); goto seed_done; } \
-    } while (0)
-        SSTEP(dalloc(&flag, (size_t)n + 1, s));
-        SSTEP(dalloc(&map, (size_t)n + 1, s));
-        SSTEP(dalloc(&cnt, (size_t)n + 1, s));
-        SSTEP(dalloc(&pos, (size_t)n + 1, s));
-        SSTEP(dalloc(&epos, (size_t)n + 1, s));
-        k_sub_flags<<<grid_n(n), 256, 0, s>>>(n, g->core2, x0, flag);
-        note_launch();
-        SSTEP(exclusive_scan_u32_to_u64(flag, pos, n, s));
-        SCU(cudaMemcpyAsync(&nh, pos + n, 8, cudaMemcpyDeviceToHost, s));
-        SCU(cudaStreamSynchronize(s));
-        SSTEP(dalloc(&orig, nh + 1, s));
-        k_sub_map<<<grid_n(n), 256, 0, s>>>(n, flag, pos, map, orig);
-        k_sub_count<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, cnt);
-        note_launch();
-        note_launch();
-        SSTEP(exclusive_scan_u32_to_u64(cnt, epos, n, s));
-        SCU(cudaMemcpyAsync(&mh, epos + n, 8, cudaMemcpyDeviceToHost, s));
-        SCU(cudaStreamSynchronize(s));
-        SSTEP(dalloc(&es, 2 * mh + 2, s));
-        k_sub_fill<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, epos, es,
-                                                           es + mh);
-        note_launch();
-        SCU(cudaGetLastError());
-        si.sub_n = (uint32_t)nh;
-        si.sub_m = mh;
-        // ---- H: CSR, order, clique-degrees, peel from level k
-        H = new (std::nothrow) dsd_graph();
-        if (!H) {
-            st = DSD_ERR_NOMEM;
-            goto seed_done;
+        SubCore S;
+        SeedRes hs;
+        memset(&hs, 0, sizeof(hs));
+        SeedRes* sr = nullptr;
+        st = sub_core_build(g, h, x0, k, &S);
+        if (st == DSD_OK) {
+            si.sub_n = (uint32_t)S.nh;
+            si.sub_m = S.mh;
+            record_peel(g, 1, S.pr);
+            st = dalloc(&sr, 1, s);
         }
-        H->stream = s;
-        H->n = (uint32_t)nh;
-        H->device = g->device;
-        SSTEP(build_csr(H, mh, es, es + mh));
-        SSTEP(ensure_order(H));
-        SSTEP(dalloc(&deg, nh + 2, s));
-        SSTEP(dalloc(&core, nh + 1, s));
-        SSTEP(dalloc(&lk, nh + 1, s));
-        SSTEP(dalloc(&lm, nh + 1, s));
-        SSTEP(dalloc(&ls, nh + 1, s));
-        SSTEP(dalloc(&sr, 1, s));
-        SSTEP(count_cliques(H, h, deg, deg + nh + 1));
-        SCU(cudaMemcpyAsync(&muh, deg + nh + 1, 8, cudaMemcpyDeviceToHost, s));
-        SCU(cudaStreamSynchronize(s));
-        SSTEP(run_peel(H, h, H->n, H->roff, H->radj, H->rsplit, H->maxdplus, deg, muh, core,
-                       nullptr, lk, ls, lm, &pr, k));
-        record_peel(g, 1, pr);
-        k_seed_select<<<1, 32, 0, s>>>(pr.nlevels, lk, ls, lm, k, Mn, E, sr);
-        note_launch();
-        SCU(cudaMemcpyAsync(&hs, sr, sizeof(hs), cudaMemcpyDeviceToHost, s));
-        SCU(cudaStreamSynchronize(s));
-        if (hs.accepted) {
-            // the two vertex sets, in caller ids (H ids ascend with caller ids)
-            uint32_t* fh = cnt;         // reuse: flags over H ids
-            uint64_t* ph = pos;         // reuse: positions
-            uint32_t* tmp = nullptr;
-            const unsigned long long* thr[2] = {&sr->kmax, &sr->best_k};
-            uint32_t* outs[2] = {kmax_core, densest};
-            uint32_t sizes[2] = {hs.kmax_core_size, hs.densest_size};
-            if (mem == DSD_MEM_HOST) SSTEP(dalloc(&tmp, nh + 1, s));
-            for (int q = 0; q < 2; q++) {
-                if (!outs[q] || nh == 0) continue;
-                k_sub_flags_core<<<grid_n(nh), 256, 0, s>>>((uint32_t)nh, H->old_of, core, thr[q], fh);
-                note_launch();
-                SSTEP(exclusive_scan_u32_to_u64(fh, ph, nh, s));
-                uint32_t* target = tmp ? tmp : outs[q];
-                k_sub_emit<<<grid_n(nh), 256, 0, s>>>((uint32_t)nh, fh, ph, orig, target);
-                note_launch();
-                SCU(cudaGetLastError());
-                if (tmp) {
-                    SCU(cudaMemcpyAsync(outs[q], tmp, (size_t)sizes[q] * 4, cudaMemcpyDeviceToHost, s));
-                    SCU(cudaStreamSynchronize(s));
-                }
-            }
-            dev_free(tmp, s);
-            SCU(cudaStreamSynchronize(s));
+        if (st == DSD_OK) {
+            k_seed_select<<<1, 32, 0, s>>>(S.pr.nlevels, S.lk, S.ls, S.lm, k, Mn, E, sr);
+            note_launch();
+            cudaError_t e = cudaMemcpyAsync(&hs, sr, sizeof(hs), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_fail(e, "seed select", __FILE__, __LINE__);
         }
-    seed_done:
-#undef SSTEP
-#undef SCU
-        if (H) dsd_graph_destroy(H);
-        void* ptrs[] = {flag, map, orig, cnt, es, pos, epos, deg, core, lk, lm, ls, sr};
-        for (void* p : ptrs) dev_free(p, s);
+        if (st == DSD_OK && hs.accepted) {
+            st = sub_core_emit(g, S, hs.kmax, hs.kmax_core_size, kmax_core, mem);
+            if (st == DSD_OK) st = sub_core_emit(g, S, hs.best_k, hs.densest_size, densest, mem);
+        }
+        dev_free(sr, s);
+        sub_core_free(&S, s);
         DSD_TRY(st);
         if (hs.accepted) {
             si.accepted = 1;

@@ -378,3 +378,51 @@ def test_checkpoint_roundtrip(L, tmp_path):
     np.savez(str(bad), state=st, header=hd)
     with pytest.raises(ValueError):
         train.load_checkpoint(str(bad))
+
+
+# ------------------------------------------------- CoreApp's top-down schedule
+
+def _check_topdown(L, orc, n, s, d, h):
+    og = orc.csr(n, s, d)
+    wcore, wk = orc.core_decompose(og, h)
+    w = orc.core_app(og, h, wcore, wk)
+    lk, _, _ = orc.level_stats(og, h, wcore)
+    core2, _ = orc.core_decompose(og, 2)
+    with L.Graph.from_edges(n, s, d) as g:
+        r = g.core_app_topdown(h)
+    sc = r["schedule"]
+    assert r["kmax"] == w["kmax"]
+    assert np.array_equal(r["kmax_core"], w["kmax_core"])
+    assert r["kmax_core_mu"] == w["kmax_core_mu"]
+    assert r["best_k"] == w["best_k"]
+    assert np.array_equal(r["densest"], w["densest"])
+    assert (r["densest_mu"], r["densest_size"]) == (w["densest_mu"], w["densest_size"])
+    assert sc["passes"] >= 1 and sc["sub_n"] <= n
+    if h > 2 and n:
+        # the last window is the edge core {core_2 >= x}; gamma_out is the
+        # largest C(core_2, h-1) outside it, and every core >= k_max sits inside
+        assert sc["sub_n"] == int(np.sum(core2 >= sc["x"]))
+        outside = core2[core2 < sc["x"]]
+        g_out = math.comb(int(outside.max()), h - 1) if outside.size else 0
+        assert sc["gamma_out"] == g_out
+        assert w["kmax"] > g_out or sc["sub_n"] == n
+        assert r["nlevels"] == int(np.sum(lk >= g_out + 1)) or sc["sub_n"] == n
+    return sc
+
+
+@pytest.mark.parametrize("h", [3, 4, 5])
+def test_topdown_equals_plain(L, orc, h):
+    n, s, d = gg.chung_lu(6000, 40000, 2.2, 500.0, seed=30 + h)
+    n, s, d, _ = gg.plant(n, s, d, 40, 0.7, seed=40 + h)
+    sc = _check_topdown(L, orc, n, s, d, h)
+    assert sc["sub_n"] < n   # the schedule stopped before the whole graph
+
+
+def test_topdown_small_and_random(L, orc):
+    _check_topdown(L, orc, 1, np.zeros(0, np.uint32), np.zeros(0, np.uint32), 3)
+    _check_topdown(L, orc, 9, np.zeros(0, np.uint32), np.zeros(0, np.uint32), 3)
+    r = np.random.default_rng(7)
+    for it in range(10):
+        n, s, d = gg.random_small(int(r.integers(20, 400)), float(r.uniform(0.02, 0.3)),
+                                  seed=int(r.integers(1 << 30)))
+        _check_topdown(L, orc, n, s, d, int(r.integers(2, 6)))
