@@ -63,6 +63,15 @@ def _load():
                                         ctypes.c_uint64, _u8p]
     lib.orc_level_stats.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u64p,
                                     _u64p, ctypes.c_uint32, _u64p, _u64p]
+    lib.orc_pattern_degrees.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
+                                        ctypes.c_int, _u8p, _u64p, _u64p]
+    lib.orc_pattern_core_decompose.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
+                                               ctypes.c_int, _u64p, _u64p]
+    lib.orc_pattern_level_stats.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
+                                            ctypes.c_int, _u64p, _u64p, ctypes.c_uint32,
+                                            _u64p, _u64p]
+    for f in ("orc_pattern_degrees", "orc_pattern_core_decompose", "orc_pattern_level_stats"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("orc_clique_degrees", "orc_vertex_clique_degree", "orc_vertex_clique_degrees",
               "orc_induced_clique_count",
               "orc_core_decompose", "orc_threshold_prune", "orc_level_stats"):
@@ -212,3 +221,72 @@ def core_app(g: Graph, h: int, core=None, kmax=None):
 
 def density(mu: int, size: int) -> Fraction:
     return Fraction(int(mu), int(size)) if size else Fraction(0)
+
+
+# ------------------------------------------------------------ patterns (Sec. 6)
+
+STAR = 1     # x-star: a centre and x of its neighbours
+LOOP4 = 2    # the 4-vertex loop (4-cycle)
+
+
+def pattern_size(pattern: int, x: int) -> int:
+    return x + 1 if pattern == STAR else 4
+
+
+def pattern_degrees(g: Graph, pattern: int, x: int = 0, alive=None):
+    """Pattern-degrees (Sec. 6) of every vertex and mu; alive: optional mask."""
+    lib = _load()
+    deg = np.zeros(max(g.n, 1), np.uint64)
+    mu = np.zeros(1, np.uint64)
+    m = None
+    if alive is not None:
+        m = np.ascontiguousarray(alive, np.uint8)
+    _check(lib.orc_pattern_degrees(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), pattern, x,
+                                   _p(m, _u8p) if m is not None else None, _p(deg, _u64p),
+                                   _p(mu, _u64p)))
+    return deg[:g.n], int(mu[0])
+
+
+def pattern_core_decompose(g: Graph, pattern: int, x: int = 0):
+    """Algorithm 3 extended to a pattern: (core numbers, k_max)."""
+    lib = _load()
+    core = np.zeros(max(g.n, 1), np.uint64)
+    km = np.zeros(1, np.uint64)
+    _check(lib.orc_pattern_core_decompose(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), pattern, x,
+                                          _p(core, _u64p), _p(km, _u64p)))
+    return core[:g.n], int(km[0])
+
+
+def pattern_level_stats(g: Graph, pattern: int, x: int, core):
+    """(levels k, |R_k|, mu(R_k)) for the distinct core values, ascending."""
+    lib = _load()
+    core = np.ascontiguousarray(core, np.uint64)
+    levels = np.unique(core) if g.n else np.zeros(0, np.uint64)
+    levels = np.ascontiguousarray(levels, np.uint64)
+    nl = levels.size
+    size = np.zeros(max(nl, 1), np.uint64)
+    mu = np.zeros(max(nl, 1), np.uint64)
+    _check(lib.orc_pattern_level_stats(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), pattern, x,
+                                       _p(core, _u64p), _p(levels, _u64p), nl, _p(size, _u64p),
+                                       _p(mu, _u64p)))
+    return levels, size[:nl], mu[:nl]
+
+
+def pattern_core_app(g: Graph, pattern: int, x: int = 0):
+    """k_max, the (k_max, Psi)-core, and the densest level set (ties to the
+    larger k) with its exact pattern-density, for a pattern (Sec. 6)."""
+    core, km = pattern_core_decompose(g, pattern, x)
+    levels, size, mu = pattern_level_stats(g, pattern, x, core)
+    if g.n == 0:
+        return dict(kmax=0, kmax_core=np.zeros(0, np.uint32), kmax_core_mu=0, best_k=0,
+                    densest=np.zeros(0, np.uint32), densest_mu=0, densest_size=0)
+    best = 0
+    for j in range(1, len(levels)):
+        if density(mu[j], size[j]) >= density(mu[best], size[best]):
+            best = j
+    bk = int(levels[best])
+    return dict(kmax=km, kmax_core=np.flatnonzero(core >= km).astype(np.uint32),
+                kmax_core_mu=int(mu[-1]), best_k=bk,
+                densest=np.flatnonzero(core >= bk).astype(np.uint32),
+                densest_mu=int(mu[best]), densest_size=int(size[best]))
+

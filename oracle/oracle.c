@@ -572,3 +572,182 @@ out:
     lister_free(&L); wg_free(&g);
     return rc;
 }
+
+/* ------------------------------------------------ pattern densities --- */
+/*
+ * Sec. 6 generalises the h-clique to a pattern Psi; an instance is a
+ * subgraph isomorphic to Psi (Def. of subgraph isomorphism there: every
+ * pattern edge maps to a graph edge, so instances need not be induced),
+ * pattern-degree deg(v, Psi) = instances containing v, mu(G, Psi) = number
+ * of instances.  Two special patterns, with the counts the appendix on
+ * special patterns derives:
+ *   ORC_STAR, x leaves (x >= 2): an instance is a centre c with x of its
+ *     neighbours; deg(v) = C(d_v, x) + sum_{u in N(v)} C(d_u - 1, x - 1)
+ *     (v as the centre, or as a leaf of a neighbour u); mu = sum_c C(d_c, x).
+ *   ORC_LOOP4, the 4-vertex loop: an instance is a 4-cycle v-a-w-b; for
+ *     fixed v its opposite vertex w and the pair {a, b} of common neighbours
+ *     determine it, so deg(v) = sum_{w != v} C(|N(v) ∩ N(w)|, 2) (the
+ *     appendix groups the 2-paths from v by their far end w); mu = sum deg / 4.
+ * Only the vertices with alive[v] != 0 (all if alive == NULL) form the graph.
+ */
+#define ORC_STAR 1
+#define ORC_LOOP4 2
+
+static uint64_t binom_u64(uint64_t a, int b) {
+    if (b < 0 || a < (uint64_t)b) return 0;
+    uint64_t c = 1;
+    for (int t = 1; t <= b; t++) c = c * (a - (uint64_t)b + (uint64_t)t) / (uint64_t)t;
+    return c;
+}
+
+static uint64_t alive_degree(const uint64_t* off, const uint32_t* adj, const uint8_t* alive,
+                             uint32_t v) {
+    uint64_t d = 0;
+    for (uint64_t p = off[v]; p < off[v + 1]; p++)
+        if (!alive || alive[adj[p]]) d++;
+    return d;
+}
+
+/* deg(v) of one alive vertex; cnt: n zeroed scratch counters (returned zeroed). */
+static uint64_t pattern_degree_one(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                                   int pattern, int x, const uint8_t* alive, uint32_t v,
+                                   uint32_t* cnt) {
+    (void)n;
+    if (pattern == ORC_STAR) {
+        uint64_t dv = alive_degree(off, adj, alive, v);
+        uint64_t s = binom_u64(dv, x);
+        for (uint64_t p = off[v]; p < off[v + 1]; p++) {
+            uint32_t u = adj[p];
+            if (alive && !alive[u]) continue;
+            s += binom_u64(alive_degree(off, adj, alive, u) - 1, x - 1);
+        }
+        return s;
+    }
+    /* ORC_LOOP4: c(v, w) by walking the 2-paths v-a-w */
+    uint64_t s = 0;
+    for (uint64_t p = off[v]; p < off[v + 1]; p++) {
+        uint32_t a = adj[p];
+        if (alive && !alive[a]) continue;
+        for (uint64_t q = off[a]; q < off[a + 1]; q++) {
+            uint32_t w = adj[q];
+            if (w == v || (alive && !alive[w])) continue;
+            s += cnt[w]++;          /* the new 2-path pairs with each earlier one */
+        }
+    }
+    for (uint64_t p = off[v]; p < off[v + 1]; p++) {
+        uint32_t a = adj[p];
+        if (alive && !alive[a]) continue;
+        for (uint64_t q = off[a]; q < off[a + 1]; q++) cnt[adj[q]] = 0;
+    }
+    return s;
+}
+
+static int check_pattern(int pattern, int x) {
+    if (pattern == ORC_STAR) return (x >= 2 && x <= 8) ? ORC_OK : ORC_EINVAL;
+    if (pattern == ORC_LOOP4) return ORC_OK;
+    return ORC_EINVAL;
+}
+
+static int pattern_size(int pattern, int x) { return pattern == ORC_STAR ? x + 1 : 4; }
+
+/* deg[v] for every vertex (0 for vertices not alive) and mu. */
+int orc_pattern_degrees(uint32_t n, const uint64_t* off, const uint32_t* adj, int pattern,
+                        int x, const uint8_t* alive, uint64_t* deg, uint64_t* mu) {
+    if (check_pattern(pattern, x)) return ORC_EINVAL;
+    uint32_t* cnt = (uint32_t*)calloc((size_t)(n ? n : 1), sizeof(uint32_t));
+    if (!cnt) return ORC_ENOMEM;
+    uint64_t total = 0;
+    for (uint32_t v = 0; v < n; v++) {
+        deg[v] = (alive && !alive[v]) ? 0 : pattern_degree_one(n, off, adj, pattern, x, alive, v, cnt);
+        total += deg[v];
+    }
+    *mu = total / (uint64_t)pattern_size(pattern, x);
+    free(cnt);
+    return ORC_OK;
+}
+
+/* Algorithm 3 extended to a pattern (Sec. 4.1 remark on k-pattern-cores):
+ * repeatedly take a vertex v of minimum pattern-degree (ties to the smaller
+ * id), set core[v] to it, and remove v; the pattern-degree of every vertex
+ * that shared an instance with v -- all lie within two hops of v -- is
+ * recomputed on the remaining graph and, as Algorithm 3 never lowers a
+ * degree below the removed vertex's, raised to at least core[v]. */
+int orc_pattern_core_decompose(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                               int pattern, int x, uint64_t* core, uint64_t* kmax) {
+    if (check_pattern(pattern, x)) return ORC_EINVAL;
+    int rc = ORC_ENOMEM;
+    size_t nn = n ? n : 1;
+    uint64_t* key = (uint64_t*)malloc(nn * sizeof(uint64_t));
+    uint8_t* alive = (uint8_t*)malloc(nn);
+    uint32_t* cnt = (uint32_t*)calloc(nn, sizeof(uint32_t));
+    uint32_t* stamp = (uint32_t*)calloc(nn, sizeof(uint32_t));
+    uint32_t* tie = (uint32_t*)malloc(nn * sizeof(uint32_t));
+    uint32_t* touched = (uint32_t*)malloc(nn * sizeof(uint32_t));
+    vheap H;
+    memset(&H, 0, sizeof(H));
+    H.heap = (uint32_t*)malloc(nn * sizeof(uint32_t));
+    H.pos = (uint32_t*)malloc(nn * sizeof(uint32_t));
+    if (!key || !alive || !cnt || !stamp || !tie || !touched || !H.heap || !H.pos) goto out;
+    for (uint32_t v = 0; v < n; v++) { alive[v] = 1; tie[v] = v; }
+    for (uint32_t v = 0; v < n; v++)
+        key[v] = pattern_degree_one(n, off, adj, pattern, x, alive, v, cnt);
+    H.key = key; H.tie = tie; H.size = n;
+    for (uint32_t i = 0; i < n; i++) { H.heap[i] = i; H.pos[i] = i; }
+    for (int64_t i = (int64_t)n / 2 - 1; i >= 0; i--) vh_down(&H, (uint32_t)i);
+    uint64_t km = 0;
+    uint32_t round = 0;
+    while (H.size) {
+        uint32_t v = vh_pop(&H);
+        uint64_t kv = key[v];
+        core[v] = kv;
+        if (kv > km) km = kv;
+        alive[v] = 0;
+        /* alive vertices within two hops of v */
+        round++;
+        uint32_t nt = 0;
+        for (uint64_t p = off[v]; p < off[v + 1]; p++) {
+            uint32_t a = adj[p];
+            if (alive[a] && stamp[a] != round) { stamp[a] = round; touched[nt++] = a; }
+            for (uint64_t q = off[a]; q < off[a + 1]; q++) {
+                uint32_t w = adj[q];
+                if (alive[w] && stamp[w] != round) { stamp[w] = round; touched[nt++] = w; }
+            }
+        }
+        for (uint32_t i = 0; i < nt; i++) {
+            uint32_t u = touched[i];
+            uint64_t d = pattern_degree_one(n, off, adj, pattern, x, alive, u, cnt);
+            if (d < kv) d = kv;
+            if (d < key[u]) {
+                key[u] = d;
+                vh_up(&H, H.pos[u]);
+            }
+        }
+    }
+    *kmax = km;
+    rc = ORC_OK;
+out:
+    free(key); free(alive); free(cnt); free(stamp); free(tie); free(touched);
+    free(H.heap); free(H.pos);
+    return rc;
+}
+
+/* For the distinct core values k (ascending, nl of them in levels[]):
+ * size[j] = |R_k| and mu[j] = mu(G[R_k], Psi) with R_k = {v : core(v) >= k}. */
+int orc_pattern_level_stats(uint32_t n, const uint64_t* off, const uint32_t* adj, int pattern,
+                            int x, const uint64_t* core, const uint64_t* levels, uint32_t nl,
+                            uint64_t* size, uint64_t* mu) {
+    if (check_pattern(pattern, x)) return ORC_EINVAL;
+    size_t nn = n ? n : 1;
+    uint8_t* mask = (uint8_t*)malloc(nn);
+    uint64_t* deg = (uint64_t*)malloc(nn * sizeof(uint64_t));
+    if (!mask || !deg) { free(mask); free(deg); return ORC_ENOMEM; }
+    int rc = ORC_OK;
+    for (uint32_t j = 0; j < nl && rc == ORC_OK; j++) {
+        uint64_t s = 0;
+        for (uint32_t v = 0; v < n; v++) { mask[v] = core[v] >= levels[j]; s += mask[v]; }
+        size[j] = s;
+        rc = orc_pattern_degrees(n, off, adj, pattern, x, mask, deg, &mu[j]);
+    }
+    free(mask); free(deg);
+    return rc;
+}
