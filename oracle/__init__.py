@@ -3,8 +3,9 @@
 Plain, slow, single-threaded implementations of what the GPU path computes,
 written from the paper (Fang et al., PVLDB 2019): clique-degrees (Def. 3),
 the (k,Psi)-core decomposition (Algorithm 3), the (k,Psi)-core by threshold
-pruning (Def. 6), level statistics of the nested cores, and the CoreApp
-outputs (Algorithms 5 and 6; Pruning1 of Sec. 5.1).
+pruning (Def. 6), level statistics of the nested cores, the CoreApp
+outputs (Algorithms 5 and 6; Pruning1 of Sec. 5.1), and the exact CDS by
+Algorithm 1 (Exact) with its minimum cuts.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -70,6 +71,9 @@ def _load():
     lib.orc_pattern_level_stats.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
                                             ctypes.c_int, _u64p, _u64p, ctypes.c_uint32,
                                             _u64p, _u64p]
+    lib.orc_exact_cds.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u8p, _u64p,
+                                  _u64p, _u32p]
+    lib.orc_exact_cds.restype = ctypes.c_int
     for f in ("orc_pattern_degrees", "orc_pattern_core_decompose", "orc_pattern_level_stats"):
         getattr(lib, f).restype = ctypes.c_int
     for f in ("orc_clique_degrees", "orc_vertex_clique_degree", "orc_vertex_clique_degrees",
@@ -221,6 +225,25 @@ def core_app(g: Graph, h: int, core=None, kmax=None):
 
 def density(mu: int, size: int) -> Fraction:
     return Fraction(int(mu), int(size)) if size else Fraction(0)
+
+
+def exact_cds(g: Graph, h: int):
+    """The CDS by Algorithm 1 (Exact): rho_opt and the largest densest set.
+
+    Returns dict(cds = sorted vertex ids of the union of all maximum-density
+    sets, mu = its h-clique count, size = its size, steps = binary-search
+    iterations); rho_opt = mu / size.  With no h-clique the answer is V with
+    density 0.
+    """
+    lib = _load()
+    mark = np.zeros(max(g.n, 1), np.uint8)
+    mu = np.zeros(1, np.uint64)
+    size = np.zeros(1, np.uint64)
+    steps = np.zeros(1, np.uint32)
+    _check(lib.orc_exact_cds(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), h, _p(mark, _u8p),
+                             _p(mu, _u64p), _p(size, _u64p), _p(steps, _u32p)))
+    cds = np.flatnonzero(mark[:g.n]).astype(np.uint32)
+    return dict(cds=cds, mu=int(mu[0]), size=int(size[0]), steps=int(steps[0]))
 
 
 # ------------------------------------------------------------ patterns (Sec. 6)

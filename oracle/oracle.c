@@ -30,6 +30,11 @@
  *                            mu(R_k), with R_k = {v : core(v) >= k} (Def. 6,
  *                            nestedness); one clique lies in R_k exactly when
  *                            its smallest member core number is >= k.
+ *   orc_exact_cds            Algorithm 1 (Exact, Sec. 3.1): binary search on
+ *                            alpha over [0, max clique-degree] with one
+ *                            minimum st-cut of the (h-1)-clique flow network
+ *                            per guess, stopping once u - l < 1/(n(n-1));
+ *                            then the largest densest vertex set.
  *
  * Clique instances are unordered vertex sets (Def. 2 and the remark after
  * Def. 3).  Each set is listed exactly once as the increasing sequence
@@ -248,6 +253,10 @@ struct lister {
     uint8_t* queued;
     uint32_t* queue;
     uint64_t qtail;
+    const uint8_t* mask;      /* count inside a vertex subset (new ids) */
+    uint32_t* store;          /* collected tuples, h entries each */
+    uint64_t nstore, capstore;
+    int overflow;
 };
 
 /* tuple[0..depth-1] is a clique; cand (sorted, ncand entries) holds every
@@ -749,5 +758,340 @@ int orc_pattern_level_stats(uint32_t n, const uint64_t* off, const uint32_t* adj
         rc = orc_pattern_degrees(n, off, adj, pattern, x, mask, deg, &mu[j]);
     }
     free(mask); free(deg);
+    return rc;
+}
+
+/* ------------------------------------------ Algorithm 1 (Exact) ------ */
+
+/* Sec. 3.1 builds, for a guess alpha, a flow network over the vertices and
+ * the (h-1)-cliques Lambda: s -> v with capacity deg(v, Psi), v -> t with
+ * capacity alpha * h, psi -> v with infinite capacity for every member v of
+ * psi, and v -> psi with capacity 1 when psi + v is an h-clique.  A vertex
+ * set A on the source side (with every psi whose members all lie in A) cuts
+ *     h * mu(G) - h * mu(A) + alpha * h * |A|,
+ * so the minimum cut lies below h * mu(G) exactly when some A has
+ * mu(A) > alpha * |A|.  Here alpha = p / q is kept exact by scaling every
+ * capacity by q (128-bit integers), and the minimum cut comes from Dinic's
+ * algorithm. */
+
+typedef unsigned __int128 u128;
+
+enum { ARC_REV = 0, ARC_S = 1, ARC_T = 2, ARC_Q = 3, ARC_INF = 4 };
+
+typedef struct {
+    uint32_t N;               /* 0 = s, 1 = t, 2 + v vertices, then Lambda */
+    uint64_t E, cap_e;
+    int64_t* head;
+    int64_t* next;
+    uint32_t* to;
+    uint8_t* kind;
+    u128* cap;
+    int32_t* level;
+    int64_t* it;
+    uint32_t* queue;
+} fnet;
+
+static void fn_free(fnet* F) {
+    free(F->head); free(F->next); free(F->to); free(F->kind); free(F->cap);
+    free(F->level); free(F->it); free(F->queue);
+    memset(F, 0, sizeof(*F));
+}
+
+static int fn_init(fnet* F, uint32_t N, uint64_t E) {
+    memset(F, 0, sizeof(*F));
+    F->N = N;
+    F->cap_e = E;
+    F->head = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    F->next = (int64_t*)malloc((size_t)(E ? E : 1) * sizeof(int64_t));
+    F->to = (uint32_t*)malloc((size_t)(E ? E : 1) * sizeof(uint32_t));
+    F->kind = (uint8_t*)malloc((size_t)(E ? E : 1));
+    F->cap = (u128*)malloc((size_t)(E ? E : 1) * sizeof(u128));
+    F->level = (int32_t*)malloc((size_t)N * sizeof(int32_t));
+    F->it = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    F->queue = (uint32_t*)malloc((size_t)N * sizeof(uint32_t));
+    if (!F->head || !F->next || !F->to || !F->kind || !F->cap || !F->level || !F->it ||
+        !F->queue) {
+        fn_free(F);
+        return ORC_ENOMEM;
+    }
+    for (uint32_t x = 0; x < N; x++) F->head[x] = -1;
+    return ORC_OK;
+}
+
+/* Arc u -> v of the given kind and its residual twin v -> u (index ^ 1). */
+static void fn_arc(fnet* F, uint32_t u, uint32_t v, uint8_t kind) {
+    uint64_t e = F->E;
+    if (e + 2 > F->cap_e) { F->E = e + 2; return; }   /* counted, caught by the caller */
+    F->to[e] = v; F->kind[e] = kind; F->next[e] = F->head[u]; F->head[u] = (int64_t)e;
+    F->to[e + 1] = u; F->kind[e + 1] = ARC_REV; F->next[e + 1] = F->head[v];
+    F->head[v] = (int64_t)(e + 1);
+    F->E = e + 2;
+}
+
+/* Capacities for alpha = p / q (all scaled by q). */
+static void fn_capacities(fnet* F, const uint64_t* deg, int h, u128 p, u128 q) {
+    const u128 inf = (u128)1 << 120;
+    for (uint64_t e = 0; e < F->E; e += 2) {
+        uint32_t u = F->to[e + 1];
+        u128 c = 0;
+        switch (F->kind[e]) {
+            case ARC_S: c = q * deg[F->to[e] - 2]; break;
+            case ARC_T: c = p * (u128)h; break;
+            case ARC_Q: c = q; break;
+            case ARC_INF: c = inf; break;
+        }
+        (void)u;
+        F->cap[e] = c;
+        F->cap[e + 1] = 0;
+    }
+}
+
+/* Breadth-first levels from s over arcs with residual capacity. */
+static int fn_bfs(fnet* F) {
+    for (uint32_t x = 0; x < F->N; x++) F->level[x] = -1;
+    uint64_t qh = 0, qt = 0;
+    F->level[0] = 0;
+    F->queue[qt++] = 0;
+    while (qh < qt) {
+        uint32_t u = F->queue[qh++];
+        for (int64_t e = F->head[u]; e >= 0; e = F->next[e]) {
+            uint32_t v = F->to[e];
+            if (F->cap[e] > 0 && F->level[v] < 0) {
+                F->level[v] = F->level[u] + 1;
+                F->queue[qt++] = v;
+            }
+        }
+    }
+    return F->level[1] >= 0;
+}
+
+/* Dinic's maximum flow from s = 0 to t = 1; the blocking flow of each level
+ * graph is found by an explicit-stack depth-first search. */
+static int fn_maxflow(fnet* F, u128* flow_out) {
+    uint32_t* pnode = (uint32_t*)malloc((size_t)F->N * sizeof(uint32_t));
+    int64_t* parc = (int64_t*)malloc((size_t)F->N * sizeof(int64_t));
+    if (!pnode || !parc) { free(pnode); free(parc); return ORC_ENOMEM; }
+    u128 flow = 0;
+    while (fn_bfs(F)) {
+        for (uint32_t x = 0; x < F->N; x++) F->it[x] = F->head[x];
+        for (;;) {
+            uint32_t depth = 0, u = 0;
+            int found = 0;
+            for (;;) {
+                if (u == 1) { found = 1; break; }
+                int64_t e = F->it[u];
+                while (e >= 0 && !(F->cap[e] > 0 && F->level[F->to[e]] == F->level[u] + 1))
+                    e = F->next[e];
+                F->it[u] = e;
+                if (e < 0) {                      /* dead end: retreat */
+                    F->level[u] = -1;
+                    if (depth == 0) break;
+                    depth--;
+                    u = pnode[depth];
+                    F->it[u] = F->next[parc[depth]];
+                    continue;
+                }
+                pnode[depth] = u;
+                parc[depth] = e;
+                depth++;
+                u = F->to[e];
+            }
+            if (!found) break;
+            u128 b = F->cap[parc[0]];
+            for (uint32_t i = 1; i < depth; i++)
+                if (F->cap[parc[i]] < b) b = F->cap[parc[i]];
+            for (uint32_t i = 0; i < depth; i++) {
+                F->cap[parc[i]] -= b;
+                F->cap[parc[i] ^ 1] += b;
+            }
+            flow += b;
+        }
+    }
+    free(pnode); free(parc);
+    *flow_out = flow;
+    return ORC_OK;
+}
+
+/* After a maximum flow: mark[x] = 1 for the nodes that can still reach t
+ * through arcs with residual capacity.  Their complement is the largest
+ * source side among all minimum cuts. */
+static void fn_reach_t(fnet* F, uint8_t* mark) {
+    memset(mark, 0, F->N);
+    uint64_t qh = 0, qt = 0;
+    mark[1] = 1;
+    F->queue[qt++] = 1;
+    while (qh < qt) {
+        uint32_t y = F->queue[qh++];
+        for (int64_t e = F->head[y]; e >= 0; e = F->next[e]) {
+            uint32_t x = F->to[e];            /* arc e: y -> x; its twin x -> y */
+            if (!mark[x] && F->cap[e ^ 1] > 0) {
+                mark[x] = 1;
+                F->queue[qt++] = x;
+            }
+        }
+    }
+}
+
+static void visit_store(lister* L, const uint32_t* c) {
+    if (L->nstore >= L->capstore) {
+        uint64_t nc = L->capstore ? 2 * L->capstore : 1024;
+        uint32_t* ns = (uint32_t*)realloc(L->store, (size_t)nc * L->h * sizeof(uint32_t));
+        if (!ns) { L->overflow = 1; return; }
+        L->store = ns;
+        L->capstore = nc;
+    }
+    memcpy(L->store + L->nstore * L->h, c, (size_t)L->h * sizeof(uint32_t));
+    L->nstore++;
+}
+
+static void visit_count_mask(lister* L, const uint32_t* c) {
+    for (int i = 0; i < L->h; i++)
+        if (!L->mask[c[i]]) return;
+    L->mu++;
+}
+
+/* mu(G[A]) for A = {new ids x : mask[x]} on the working graph. */
+static int wg_count_in(const wgraph* g, int h, const uint8_t* mask, uint64_t* mu) {
+    lister L;
+    if (lister_init(&L, g, h, visit_count_mask)) { lister_free(&L); return ORC_ENOMEM; }
+    L.mask = mask;
+    list_all(&L);
+    *mu = L.mu;
+    lister_free(&L);
+    return ORC_OK;
+}
+
+static u128 gcd128(u128 a, u128 b) {
+    while (b) { u128 t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* The CDS of G (Problem 1) by Algorithm 1, and then the largest densest set.
+ *
+ * in_cds[v] (original ids) marks the union of all vertex sets of maximum
+ * h-clique-density; *mu_out = mu of that set and *size_out = its size, so
+ * rho_opt = *mu_out / *size_out.  *steps = binary-search iterations.  The
+ * union of two densest sets is again densest (mu(A u B) + mu(A n B) >=
+ * mu(A) + mu(B)), so this set is unique; it is the largest source side of a
+ * minimum cut at alpha = rho_opt.  With no h-clique every set has density 0
+ * and the answer is V.  Returns ORC_EINVAL when n^2 * max deg(v, Psi) does
+ * not fit the exact arithmetic (2^60). */
+int orc_exact_cds(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
+                  uint8_t* in_cds, uint64_t* mu_out, uint64_t* size_out, uint32_t* steps) {
+    if (check_h(h)) return ORC_EINVAL;
+    *steps = 0;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    int rc = ORC_ENOMEM;
+    lister L, C;
+    memset(&L, 0, sizeof(L));
+    memset(&C, 0, sizeof(C));
+    fnet F;
+    memset(&F, 0, sizeof(F));
+    uint64_t* deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    uint8_t* inD = (uint8_t*)calloc((size_t)(n ? n : 1), 1);
+    uint8_t* mark = NULL;
+    uint32_t* cn = (uint32_t*)malloc(((size_t)g.maxdeg + 1) * sizeof(uint32_t));
+    uint32_t* cn2 = (uint32_t*)malloc(((size_t)g.maxdeg + 1) * sizeof(uint32_t));
+    if (!deg || !inD || !cn || !cn2) goto out;
+    /* clique-degrees and mu(G) */
+    if (lister_init(&L, &g, h, visit_count)) goto out;
+    L.deg = deg;
+    list_all(&L);
+    uint64_t mu = L.mu;
+    if (mu == 0) {
+        for (uint32_t v = 0; v < n; v++) in_cds[v] = 1;
+        *mu_out = 0;
+        *size_out = n;
+        rc = ORC_OK;
+        goto out;
+    }
+    uint64_t maxdeg = 0;
+    for (uint32_t v = 0; v < n; v++) if (deg[v] > maxdeg) maxdeg = deg[v];
+    u128 nn1 = (u128)n * (n - 1);
+    if (nn1 * maxdeg >= ((u128)1 << 60)) { rc = ORC_EINVAL; goto out; }
+    /* Lambda: the (h-1)-cliques, each once */
+    if (lister_init(&C, &g, h - 1, visit_store)) goto out;
+    list_all(&C);
+    if (C.overflow) goto out;
+    uint64_t nl = C.nstore;
+    if ((uint64_t)n + nl + 2 >= ((uint64_t)1 << 31)) { rc = ORC_EINVAL; goto out; }
+    uint32_t N = (uint32_t)(2 + n + nl);
+    uint64_t E = 2 * (2 * (uint64_t)n + (uint64_t)(h - 1) * nl + (uint64_t)h * mu);
+    if (fn_init(&F, N, E)) goto out;
+    mark = (uint8_t*)malloc(N);
+    if (!mark) goto out;
+    for (uint32_t v = 0; v < n; v++) {
+        fn_arc(&F, 0, 2 + v, ARC_S);
+        fn_arc(&F, 2 + v, 1, ARC_T);
+    }
+    for (uint64_t i = 0; i < nl; i++) {
+        const uint32_t* psi = C.store + i * (h - 1);
+        uint32_t node = (uint32_t)(2 + n + i);
+        for (int j = 0; j < h - 1; j++) fn_arc(&F, node, 2 + psi[j], ARC_INF);
+        /* common neighbours of psi's members: psi + w is an h-clique */
+        uint32_t x0 = psi[0];
+        uint32_t k = (uint32_t)(g.off[x0 + 1] - g.off[x0]);
+        memcpy(cn, g.adj + g.off[x0], (size_t)k * sizeof(uint32_t));
+        for (int j = 1; j < h - 1 && k; j++) {
+            uint32_t x = psi[j];
+            k = intersect(cn, k, g.adj + g.off[x], g.off[x + 1] - g.off[x], cn2);
+            memcpy(cn, cn2, (size_t)k * sizeof(uint32_t));
+        }
+        for (uint32_t j = 0; j < k; j++) fn_arc(&F, 2 + cn[j], node, ARC_Q);
+    }
+    if (F.E != E) { rc = -3; goto out; }
+    /* binary search (l, u) = (L, U) / 2^t over [0, max deg] */
+    u128 Lo = 0, Up = maxdeg;
+    int t = 0, haveD = 0;
+    while ((Up - Lo) * nn1 >= ((u128)1 << t)) {
+        u128 A = Lo + Up;               /* alpha = A / 2^(t+1) */
+        u128 q = (u128)1 << (t + 1);
+        fn_capacities(&F, deg, h, A, q);
+        u128 flow;
+        if (fn_maxflow(&F, &flow)) goto out;
+        /* minimal source side: the nodes s still reaches (last BFS) */
+        int any = 0;
+        for (uint32_t v = 0; v < n; v++) if (F.level[2 + v] >= 0) { any = 1; break; }
+        if (!any) {
+            Up = A;
+            Lo = 2 * Lo;
+        } else {
+            Lo = A;
+            Up = 2 * Up;
+            for (uint32_t v = 0; v < n; v++) inD[v] = F.level[2 + v] >= 0;
+            haveD = 1;
+        }
+        t++;
+        (*steps)++;
+        if (t > 120) { rc = -3; goto out; }
+    }
+    if (!haveD) { rc = -3; goto out; }
+    uint64_t muD, sD = 0;
+    for (uint32_t v = 0; v < n; v++) sD += inD[v];
+    if (wg_count_in(&g, h, inD, &muD)) goto out;
+    /* the largest densest set: the largest minimum-cut source side at
+     * alpha = rho(D) = rho_opt */
+    u128 gg = gcd128(muD, sD);
+    fn_capacities(&F, deg, h, (u128)muD / gg, (u128)sD / gg);
+    u128 flow;
+    if (fn_maxflow(&F, &flow)) goto out;
+    if (flow != (u128)sD / gg * h * mu) { rc = -3; goto out; }  /* no set beats rho(D) */
+    fn_reach_t(&F, mark);
+    uint64_t sM = 0, muM = 0;
+    for (uint32_t v = 0; v < n; v++) { inD[v] = !mark[2 + v]; sM += inD[v]; }
+    if (wg_count_in(&g, h, inD, &muM)) goto out;
+    if (sM < sD || (u128)muM * sD != (u128)muD * sM) { rc = -3; goto out; }
+    for (uint32_t i = 0; i < n; i++) in_cds[g.old_of[i]] = inD[i];
+    *mu_out = muM;
+    *size_out = sM;
+    rc = ORC_OK;
+out:
+    fn_free(&F);
+    free(C.store);
+    lister_free(&C);
+    lister_free(&L);
+    free(deg); free(inD); free(mark); free(cn); free(cn2);
+    wg_free(&g);
     return rc;
 }
