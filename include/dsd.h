@@ -275,6 +275,44 @@ typedef struct {
 dsd_status dsd_core_app_topdown(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* densest,
                                 int mem, dsd_core_app_result* r, dsd_topdown_info* info);
 
+/* ------------------------------------------------------------ CoreExact */
+
+typedef struct {
+    uint64_t mu;              /* h-cliques inside the CDS */
+    uint32_t size;            /* |CDS|; rho_opt = mu / size exactly */
+    uint32_t cuts;            /* minimum cuts solved */
+    uint64_t k1;              /* Pruning1: ceil(rho') of the densest level */
+    uint64_t k2;              /* Pruning2: ceil of the starting lower bound */
+    uint64_t lower_mu;        /* the lower bound the search started from, */
+    uint32_t lower_size;      /*   lower_mu / lower_size */
+    uint32_t components;      /* connected components of the (k1,Psi)-core */
+    uint32_t net_nodes;       /* the first (largest) flow network: nodes */
+    uint32_t reserved;
+    uint64_t net_arcs;        /*   and arcs, residual twins included */
+    uint64_t rounds;          /* push/relabel rounds, all cuts */
+    uint64_t relabels;        /* global relabels (searches back from t), all cuts */
+} dsd_exact_info;
+
+/* CoreExact (Algorithm 4, Sec. 4.3): the h-clique densest subgraph (CDS,
+ * Problem 1) exactly.  Pruning1 locates it in the (ceil(rho'),Psi)-core
+ * (rho': density of the densest level, Sec. 4.3 lemma on the CDS's core);
+ * Pruning2 raises the lower bound to the densest connected component of
+ * that core; then minimum cuts of Algorithm 1's network (built from the
+ * (h-1)-cliques of the located core, which shrinks as the bound rises) and
+ * Dinkelbach's iteration on exact rationals reach rho_opt.
+ *   cds (capacity n, may be NULL): the largest densest vertex set -- the
+ *       union of all vertex sets of density rho_opt, itself of that density
+ *       -- ascending, host or device memory per mem.
+ *   info (not NULL): info->mu / info->size = rho_opt, plus search statistics.
+ * With no h-clique every set has density 0 and the answer is V (0 / n).
+ * Runs (or reuses) the decomposition behind dsd_core_decompose for this h.
+ * Errors: DSD_ERR_INVALID; DSD_ERR_NOMEM; DSD_ERR_UNSUPPORTED (a network
+ * of 2^31 nodes or more); DSD_ERR_OVERFLOW (scaled capacities reach 2^61);
+ * DSD_ERR_TIMEOUT (a cut ran past 4N + 100000 push/relabel rounds or the
+ * wait limit of dsd_set_wait_limit_ms); DSD_ERR_INTERNAL (a self-check of
+ * the network or of the cut failed); DSD_ERR_CUDA. */
+dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact_info* info);
+
 /* ------------------------------------------------------------- batches */
 
 /* Many small graphs in one launch.  The paper treats one graph at a time;

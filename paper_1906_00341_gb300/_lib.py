@@ -46,6 +46,15 @@ class TopdownInfo(ctypes.Structure):
                 ("gamma_out", ctypes.c_uint64), ("sub_m", ctypes.c_uint64)]
 
 
+class ExactInfo(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_uint64), ("size", ctypes.c_uint32), ("cuts", ctypes.c_uint32),
+                ("k1", ctypes.c_uint64), ("k2", ctypes.c_uint64), ("lower_mu", ctypes.c_uint64),
+                ("lower_size", ctypes.c_uint32), ("components", ctypes.c_uint32),
+                ("net_nodes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("net_arcs", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("relabels", ctypes.c_uint64)]
+
+
 class SeedInfo(ctypes.Structure):
     _fields_ = [("rho_prime", ctypes.c_float), ("accepted", ctypes.c_uint32),
                 ("seed_k", ctypes.c_uint64), ("x0", ctypes.c_uint64),
@@ -105,6 +114,7 @@ SIGNATURES = {
                                    ctypes.POINTER(SeedInfo)]),
     "dsd_core_app_topdown": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult),
                                     ctypes.POINTER(TopdownInfo)]),
+    "dsd_core_exact": (_int, [_P, _int, _P, _int, ctypes.POINTER(ExactInfo)]),
 }
 
 PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
@@ -382,6 +392,12 @@ def dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem):
     return r, info
 
 
+def dsd_core_exact(g, h, cds_ptr, mem):
+    info = ExactInfo()
+    _check(load().dsd_core_exact(g, h, cds_ptr, mem, ctypes.byref(info)))
+    return info
+
+
 def dsd_core_app_topdown(g, h, kcore_ptr, densest_ptr, mem):
     r = CoreAppResult()
     info = TopdownInfo()
@@ -630,6 +646,15 @@ class Graph:
             out["densest"] = de[: r.densest_size]
         out["schedule"] = dict(passes=int(info.passes), sub_n=int(info.sub_n), x=int(info.x),
                                gamma_out=int(info.gamma_out), sub_m=int(info.sub_m))
+        return out
+
+    def core_exact(self, h, mem="host", sets=True):
+        """CoreExact: rho_opt = mu / size and the largest densest set."""
+        cds = self._alloc(self.n, 4, mem) if sets else None
+        info = dsd_core_exact(self.handle, h, self._ptr(cds) if sets else 0, self._memc(mem))
+        out = {f: int(getattr(info, f)) for f, _ in ExactInfo._fields_ if f != "reserved"}
+        if sets:
+            out["cds"] = cds[: info.size]
         return out
 
     def set_profiling(self, on=True):

@@ -308,6 +308,13 @@ __global__ void k_expand_rows(uint32_t n, const uint64_t* off, uint32_t* src) {
 }
 
 }  // namespace
+
+// Core numbers of the cached decomposition for h (caller ids), or null.
+const uint64_t* cached_core(const dsd_graph* g, int h) {
+    if (h == 2) return g->ordered ? g->core2 : nullptr;
+    return g->last_h == h ? g->core : nullptr;
+}
+
 }  // namespace dsd
 
 using namespace dsd;

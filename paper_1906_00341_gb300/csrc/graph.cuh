@@ -107,6 +107,11 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
 // level record is then (kstart - 1, |V|, mu) and the core numbers it assigns
 // are not core numbers.  Levels at or above kstart are exact.
 
+// G[{v : flag[v] != 0}] (flag: device, n entries) as a graph of its own, ids
+// ascending with g's ids; *orig (device, |H| entries) maps H ids to g ids.
+// The caller destroys *H and frees *orig (dev_free on g's stream).
+dsd_status induced_subgraph(dsd_graph* g, const uint32_t* flag, dsd_graph** H, uint32_t** orig);
+
 // The edge core {core_2 >= x0} of g as a graph of its own (ids ascend with
 // g's ids), its h-clique counts, and its peel from level kstart (levels at or
 // above kstart exact).  Used by the seeded and the top-down CoreApp calls.

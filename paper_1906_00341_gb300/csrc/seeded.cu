@@ -203,12 +203,81 @@ void sub_core_free(SubCore* S, cudaStream_t s) {
     *S = SubCore();
 }
 
+dsd_status induced_subgraph(dsd_graph* g, const uint32_t* flag, dsd_graph** Hout,
+                            uint32_t** orig_out) {
+    *Hout = nullptr;
+    *orig_out = nullptr;
+    cudaStream_t s = g->stream;
+    const uint32_t n = g->n;
+    uint32_t *map = nullptr, *cnt = nullptr, *es = nullptr, *orig = nullptr;
+    uint64_t *pos = nullptr, *epos = nullptr;
+    uint64_t nh = 0, mh = 0;
+    dsd_graph* H = nullptr;
+    dsd_status st = DSD_OK;
+    cudaError_t e = cudaSuccess;
+#define SSTEP(x)                         \
+    do {                                 \
+        st = (x);                        \
+        if (st != DSD_OK) goto done;     \
+    } while (0)
+#define SCU(x)                                                                          \
+    do {                                                                                \
+        e = (x);                                                                        \
+        if (e != cudaSuccess) { st = cuda_fail(e, #x, __FILE__, __LINE__); goto done; } \
+    } while (0)
+    SSTEP(dalloc(&map, (size_t)n + 1, s));
+    SSTEP(dalloc(&cnt, (size_t)n + 1, s));
+    SSTEP(dalloc(&pos, (size_t)n + 1, s));
+    SSTEP(dalloc(&epos, (size_t)n + 1, s));
+    SSTEP(exclusive_scan_u32_to_u64(flag, pos, n, s));
+    SCU(cudaMemcpyAsync(&nh, pos + n, 8, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    SSTEP(dalloc(&orig, nh + 1, s));
+    if (n) {
+        k_sub_map<<<grid_n(n), 256, 0, s>>>(n, flag, pos, map, orig);
+        k_sub_count<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, cnt);
+        note_launch();
+        note_launch();
+    }
+    SSTEP(exclusive_scan_u32_to_u64(cnt, epos, n, s));
+    SCU(cudaMemcpyAsync(&mh, epos + n, 8, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    SSTEP(dalloc(&es, 2 * mh + 2, s));
+    if (n) {
+        k_sub_fill<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, epos, es,
+                                                           es + mh);
+        note_launch();
+    }
+    SCU(cudaGetLastError());
+    H = new (std::nothrow) dsd_graph();
+    if (!H) {
+        st = DSD_ERR_NOMEM;
+        goto done;
+    }
+    H->stream = s;
+    H->n = (uint32_t)nh;
+    H->device = g->device;
+    SSTEP(build_csr(H, mh, es, es + mh));
+done:
+#undef SSTEP
+#undef SCU
+    void* ptrs[] = {map, cnt, es, pos, epos};
+    for (void* p : ptrs) dev_free(p, s);
+    if (st != DSD_OK) {
+        if (H) dsd_graph_destroy(H);
+        dev_free(orig, s);
+        return st;
+    }
+    *Hout = H;
+    *orig_out = orig;
+    return DSD_OK;
+}
+
 dsd_status sub_core_build(dsd_graph* g, int h, uint64_t x0, uint64_t kstart, SubCore* S) {
     *S = SubCore();
     cudaStream_t s = g->stream;
     const uint32_t n = g->n;
-    uint32_t *flag = nullptr, *map = nullptr, *cnt = nullptr, *es = nullptr;
-    uint64_t *pos = nullptr, *epos = nullptr;
+    uint32_t* flag = nullptr;
     unsigned long long* deg = nullptr;
     dsd_status st = DSD_OK;
     cudaError_t e = cudaSuccess;
@@ -223,43 +292,13 @@ dsd_status sub_core_build(dsd_graph* g, int h, uint64_t x0, uint64_t kstart, Sub
         if (e != cudaSuccess) { st = cuda_fail(e, #x, __FILE__, __LINE__); goto done; } \
     } while (0)
     SSTEP(dalloc(&flag, (size_t)n + 1, s));
-    SSTEP(dalloc(&map, (size_t)n + 1, s));
-    SSTEP(dalloc(&cnt, (size_t)n + 1, s));
-    SSTEP(dalloc(&pos, (size_t)n + 1, s));
-    SSTEP(dalloc(&epos, (size_t)n + 1, s));
     if (n) {
         k_sub_flags<<<grid_n(n), 256, 0, s>>>(n, g->core2, x0, flag);
         note_launch();
     }
-    SSTEP(exclusive_scan_u32_to_u64(flag, pos, n, s));
-    SCU(cudaMemcpyAsync(&S->nh, pos + n, 8, cudaMemcpyDeviceToHost, s));
-    SCU(cudaStreamSynchronize(s));
-    SSTEP(dalloc(&S->orig, S->nh + 1, s));
-    if (n) {
-        k_sub_map<<<grid_n(n), 256, 0, s>>>(n, flag, pos, map, S->orig);
-        k_sub_count<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, cnt);
-        note_launch();
-        note_launch();
-    }
-    SSTEP(exclusive_scan_u32_to_u64(cnt, epos, n, s));
-    SCU(cudaMemcpyAsync(&S->mh, epos + n, 8, cudaMemcpyDeviceToHost, s));
-    SCU(cudaStreamSynchronize(s));
-    SSTEP(dalloc(&es, 2 * S->mh + 2, s));
-    if (n) {
-        k_sub_fill<<<grid_n((uint64_t)n * 32), 256, 0, s>>>(n, g->off, g->adj, map, epos, es,
-                                                           es + S->mh);
-        note_launch();
-    }
-    SCU(cudaGetLastError());
-    S->H = new (std::nothrow) dsd_graph();
-    if (!S->H) {
-        st = DSD_ERR_NOMEM;
-        goto done;
-    }
-    S->H->stream = s;
-    S->H->n = (uint32_t)S->nh;
-    S->H->device = g->device;
-    SSTEP(build_csr(S->H, S->mh, es, es + S->mh));
+    SSTEP(induced_subgraph(g, flag, &S->H, &S->orig));
+    S->nh = S->H->n;
+    S->mh = S->H->m;
     SSTEP(ensure_order(S->H));
     SSTEP(dalloc(&deg, S->nh + 2, s));
     SSTEP(dalloc(&S->core, S->nh + 1, s));
@@ -274,8 +313,8 @@ dsd_status sub_core_build(dsd_graph* g, int h, uint64_t x0, uint64_t kstart, Sub
 done:
 #undef SSTEP
 #undef SCU
-    void* ptrs[] = {flag, map, cnt, es, pos, epos, deg};
-    for (void* p : ptrs) dev_free(p, s);
+    dev_free(flag, s);
+    dev_free(deg, s);
     if (st != DSD_OK) sub_core_free(S, s);
     return st;
 }

@@ -67,4 +67,6 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
     rc = lib.dsd_core_app(None, 3, None, None, 0, None)
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
+    rc = lib.dsd_core_exact(None, 3, None, 0, None)
+    assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
     lib.dsd_graph_destroy(None)   # NULL-safe
