@@ -291,6 +291,10 @@ typedef struct {
     uint64_t net_arcs;        /*   and arcs, residual twins included */
     uint64_t rounds;          /* push/relabel rounds, all cuts */
     uint64_t relabels;        /* global relabels (searches back from t), all cuts */
+    uint64_t locate_ns;       /* host wall time: decomposition lookup, Pruning2 */
+    uint64_t build_ns;        /*   located cores and their networks */
+    uint64_t cut_ns;          /*   minimum cuts */
+    uint64_t verify_ns;       /*   recount of the answer and its output */
 } dsd_exact_info;
 
 /* CoreExact (Algorithm 4, Sec. 4.3): the h-clique densest subgraph (CDS,

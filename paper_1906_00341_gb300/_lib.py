@@ -52,7 +52,9 @@ class ExactInfo(ctypes.Structure):
                 ("lower_size", ctypes.c_uint32), ("components", ctypes.c_uint32),
                 ("net_nodes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("net_arcs", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
-                ("relabels", ctypes.c_uint64)]
+                ("relabels", ctypes.c_uint64), ("locate_ns", ctypes.c_uint64),
+                ("build_ns", ctypes.c_uint64), ("cut_ns", ctypes.c_uint64),
+                ("verify_ns", ctypes.c_uint64)]
 
 
 class SeedInfo(ctypes.Structure):

@@ -39,6 +39,15 @@ namespace {
 constexpr uint32_t kUnset = 0xffffffffu;
 constexpr unsigned long long kInfCap = 1ull << 62;
 enum : uint8_t { kArcRev = 0, kArcS = 1, kArcT = 2, kArcQ = 3, kArcInf = 4 };
+// An arc's kind byte: its own kind (low 4 bits) and the kind of the forward
+// arc of its pair (high 4 bits), so the pair's total capacity -- and with it
+// the twin's residual, total minus this arc's residual -- is known locally.
+__host__ __device__ constexpr uint8_t arc_kind(uint8_t own, uint8_t pair) {
+    return (uint8_t)(own | (pair << 4));
+}
+// Arcs per node above which a block, not a warp, works on the node.
+constexpr uint64_t kBigArcs = 2048;
+constexpr int kBigThreads = 256;
 
 unsigned grid_for_n(uint64_t n, unsigned per_block = 256) {
     uint64_t b = (n + per_block - 1) / per_block;
@@ -276,10 +285,10 @@ __global__ void k_psi(uint64_t npsi, int r, const uint32_t* P, uint32_t nW, cons
                     uint64_t bpos = head[2 + w] + atomicAdd(&cursor[w], 1ull);
                     if (a < head[node + 1] && bpos < head[2 + w + 1]) {
                         to[a] = 2 + w;
-                        kind[a] = kArcRev;
+                        kind[a] = arc_kind(kArcRev, kArcQ);
                         rev[a] = bpos;
                         to[bpos] = (uint32_t)node;
-                        kind[bpos] = kArcQ;
+                        kind[bpos] = arc_kind(kArcQ, kArcQ);
                         rev[bpos] = a;
                     } else {
                         atomicOr(err, 1u);
@@ -300,10 +309,10 @@ __global__ void k_psi(uint64_t npsi, int r, const uint32_t* P, uint32_t nW, cons
             uint64_t bpos = head[2 + u] + atomicAdd(&cursor[u], 1ull);
             if (a < head[node + 1] && bpos < head[2 + u + 1]) {
                 to[a] = 2 + u;
-                kind[a] = kArcInf;
+                kind[a] = arc_kind(kArcInf, kArcInf);
                 rev[a] = bpos;
                 to[bpos] = (uint32_t)node;
-                kind[bpos] = kArcRev;
+                kind[bpos] = arc_kind(kArcRev, kArcInf);
                 rev[bpos] = a;
             } else {
                 atomicOr(err, 1u);
@@ -332,10 +341,10 @@ __global__ void k_fixed_arcs(uint32_t nW, const uint64_t* head, uint32_t* to, ui
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nW;
          v += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t sa = head[0] + v, ta = head[1] + v, v0 = head[2 + v], v1 = v0 + 1;
-        to[sa] = 2 + (uint32_t)v; kind[sa] = kArcS; rev[sa] = v0;
-        to[v0] = 0;               kind[v0] = kArcRev; rev[v0] = sa;
-        to[v1] = 1;               kind[v1] = kArcT; rev[v1] = ta;
-        to[ta] = 2 + (uint32_t)v; kind[ta] = kArcRev; rev[ta] = v1;
+        to[sa] = 2 + (uint32_t)v; kind[sa] = arc_kind(kArcS, kArcS);   rev[sa] = v0;
+        to[v0] = 0;               kind[v0] = arc_kind(kArcRev, kArcS); rev[v0] = sa;
+        to[v1] = 1;               kind[v1] = arc_kind(kArcT, kArcT);   rev[v1] = ta;
+        to[ta] = 2 + (uint32_t)v; kind[ta] = arc_kind(kArcRev, kArcT); rev[ta] = v1;
         cursor[v] = 2;
     }
 }
@@ -354,7 +363,7 @@ __global__ void k_caps(uint64_t E, const uint8_t* kind, const uint32_t* to,
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < E;
          a += (uint64_t)gridDim.x * blockDim.x) {
         unsigned long long c = 0;
-        switch (kind[a]) {
+        switch (kind[a] & 15) {
             case kArcS: c = q * vdeg[to[a] - 2]; break;
             case kArcT: c = p * (unsigned long long)h; break;
             case kArcQ: c = q; break;
@@ -369,14 +378,67 @@ __global__ void k_caps(uint64_t E, const uint8_t* kind, const uint32_t* to,
 // Heights obey h(x) <= h(y) + 1 on every residual arc x -> y; a node with
 // excess and height < N is active.  One round: every active node pushes what
 // it holds along admissible arcs (h(y) = h(x) - 1) against the heights of
-// the round's start, then each node still holding excess is relabelled to
-// 1 + the least height over its residual arcs, read from the same snapshot
-// and written to a separate buffer.  A push on x -> y needs h(x) = h(y) + 1
-// and one on y -> x the reverse, so no arc pair is pushed from both ends in
-// a round.  Every few rounds the heights are replaced by exact residual
-// distances to t (backward breadth-first search), nodes that cannot reach t
-// getting N.  With no active node left the preflow is maximum, and the nodes
-// that still reach t form the smallest sink side of a minimum cut.
+// the round's start; a node whose arcs hold no admissible one any more and
+// that still has excess is relabelled to 1 + the least height over its
+// residual arcs, read from the same snapshot and written to a separate
+// buffer.  A push on x -> y needs h(x) = h(y) + 1 and one on y -> x the
+// reverse, so no arc pair is pushed from both ends in a round.
+// Each node keeps a current arc: the arcs before it are saturated or not
+// admissible, and stay so until the node's height changes (an arc x -> y
+// turns admissible only if h(y) falls or y pushes back, which needs
+// h(y) = h(x) + 1), so a push resumes there and a relabel resets it.
+// Every few rounds the heights are replaced by exact residual distances to t
+// (backward breadth-first search; nodes that cannot reach t get N), which
+// resets all current arcs.  With no active node left the preflow is maximum,
+// and the nodes that still reach t form the smallest sink side of a minimum
+// cut.  Nodes with more than kBigArcs arcs (the core's vertices, each in
+// many cliques) are worked on by a block, the rest by a warp.
+
+struct PR {
+    const uint64_t* head;
+    const uint32_t* to;
+    const uint64_t* rev;
+    const uint8_t* kind;
+    unsigned long long* cf;
+    unsigned long long* excess;
+    uint32_t* height;
+    uint64_t* cur;
+    const unsigned long long* vdeg;
+    unsigned long long p, q;
+    int h;
+    uint64_t N;
+};
+
+// Capacity of the pair of arc e (owner -> x): the twin's residual is this
+// minus e's residual.
+__device__ __forceinline__ unsigned long long pair_cap(const PR& P, uint8_t k, uint32_t owner,
+                                                       uint32_t x) {
+    switch (k >> 4) {
+        case kArcS: return P.q * P.vdeg[(x == 0 ? owner : x) - 2];
+        case kArcT: return P.p * (unsigned long long)P.h;
+        case kArcQ: return P.q;
+        case kArcInf: return kInfCap;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ bool is_big(const PR& P, uint32_t x) {
+    return P.head[x + 1] - P.head[x] > kBigArcs;
+}
+
+__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
+    unsigned long long c = a + b;
+    return c < a ? ~0ull : c;
+}
+
+__device__ __forceinline__ unsigned long long warp_scan_sat(unsigned long long v) {
+    unsigned lane = lane_id();
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v = sat_add(v, y);
+    }
+    return v;
+}
 
 __global__ void k_preflow(uint32_t nW, const uint64_t* head, const uint64_t* rev,
                           unsigned long long* cf, unsigned long long* excess) {
@@ -390,128 +452,208 @@ __global__ void k_preflow(uint32_t nW, const uint64_t* head, const uint64_t* rev
     }
 }
 
-__global__ void k_bfs_init(uint64_t N, uint32_t* height, uint32_t* frontier, uint32_t* nf) {
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
+// Frontier lists: small nodes (warp each) and big nodes (block each); the
+// counters c[0], c[1] hold their lengths.
+__global__ void k_bfs_init(PR P, uint32_t* fs, uint32_t* fb, uint32_t* c) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.N;
          x += (uint64_t)gridDim.x * blockDim.x)
-        height[x] = x == 1 ? 0u : kUnset;
+        P.height[x] = x == 1 ? 0u : kUnset;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        frontier[0] = 1;
-        *nf = 1;
+        bool big = is_big(P, 1);
+        (big ? fb : fs)[0] = 1;
+        c[0] = big ? 0u : 1u;
+        c[1] = big ? 1u : 0u;
     }
 }
 
-// Warp per frontier node y at distance d: every x with residual x -> y (the
-// twin of y -> x) and no distance yet gets d + 1.  s is never entered.
-__global__ void k_bfs_step(const uint32_t* fin, const uint32_t* nfin, uint32_t* fout,
-                           uint32_t* nfout, uint32_t d, const uint64_t* head, const uint32_t* to,
-                           const uint64_t* rev, const unsigned long long* cf, uint32_t* height) {
+// Arc e of frontier node y at distance d: x = to[e] gets d + 1 when
+// x -> y has residual capacity and x has no distance yet (s is never entered).
+__device__ __forceinline__ void bfs_arc(const PR& P, uint32_t y, uint64_t e, uint64_t end,
+                                        uint32_t d, uint32_t* os, uint32_t* ob, uint32_t* oc) {
+    bool add = false;
+    uint32_t x = 0;
+    if (e < end) {
+        x = P.to[e];
+        if (x != 0 && P.height[x] == kUnset && pair_cap(P, P.kind[e], y, x) > P.cf[e])
+            add = atomicCAS(&P.height[x], kUnset, d + 1) == kUnset;
+    }
+    bool big = add && is_big(P, x);
+    warp_append(add && !big, x, os, oc);
+    warp_append(big, x, ob, oc + 1);
+}
+
+__global__ void k_bfs_small(PR P, const uint32_t* fs, const uint32_t* c, uint32_t d,
+                            uint32_t* os, uint32_t* ob, uint32_t* oc) {
     uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned lane = lane_id();
-    const uint32_t n_in = *nfin;
-    for (uint64_t i = gw; i < n_in; i += nw) {
-        uint32_t y = fin[i];
-        for (uint64_t p0 = head[y]; p0 < head[y + 1]; p0 += 32) {
-            uint64_t e = p0 + lane;
-            bool add = false;
-            uint32_t x = 0;
-            if (e < head[y + 1]) {
-                x = to[e];
-                if (x != 0 && cf[rev[e]] > 0 && height[x] == kUnset)
-                    add = atomicCAS(&height[x], kUnset, d + 1) == kUnset;
-            }
-            warp_append(add, x, fout, nfout);
-        }
+    const uint32_t n = c[0];
+    for (uint64_t i = gw; i < n; i += nw) {
+        uint32_t y = fs[i];
+        const uint64_t end = P.head[y + 1];
+        for (uint64_t p0 = P.head[y]; p0 < end; p0 += 32)
+            bfs_arc(P, y, p0 + lane_id(), end, d, os, ob, oc);
     }
 }
 
-__global__ void k_bfs_finish(uint64_t N, uint32_t* height) {
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
-         x += (uint64_t)gridDim.x * blockDim.x)
-        if (x == 0 || height[x] == kUnset) height[x] = (uint32_t)N;
+__global__ void k_bfs_big(PR P, const uint32_t* fb, const uint32_t* c, uint32_t d,
+                          uint32_t* os, uint32_t* ob, uint32_t* oc) {
+    const uint32_t n = c[1];
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        uint32_t y = fb[i];
+        const uint64_t end = P.head[y + 1];
+        for (uint64_t p0 = P.head[y]; p0 < end; p0 += blockDim.x)
+            bfs_arc(P, y, p0 + threadIdx.x, end, d, os, ob, oc);
+    }
 }
 
-__global__ void k_collect(uint64_t N, const unsigned long long* excess, const uint32_t* height,
-                          uint32_t* list, uint32_t* nlist) {
-    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < N;
+// Unreached nodes (and s) get N; every current arc goes back to the start.
+__global__ void k_bfs_finish(PR P) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < P.N;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        if (x == 0 || P.height[x] == kUnset) P.height[x] = (uint32_t)P.N;
+        P.cur[x] = P.head[x];
+    }
+}
+
+// Active nodes into the small (c[0]) and big (c[1]) lists.
+__global__ void k_collect(PR P, uint32_t* ls, uint32_t* lb, uint32_t* c) {
+    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < P.N;
          x0 += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t x = x0 + threadIdx.x;
-        bool act = x >= 2 && x < N && excess[x] > 0 && height[x] < N;
-        warp_append(act, (uint32_t)x, list, nlist);
+        bool act = x >= 2 && x < P.N && P.excess[x] > 0 && P.height[x] < P.N;
+        bool big = act && is_big(P, (uint32_t)x);
+        warp_append(act && !big, (uint32_t)x, ls, c);
+        warp_append(big, (uint32_t)x, lb, c + 1);
     }
 }
 
-__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
-    unsigned long long c = a + b;
-    return c < a ? ~0ull : c;
+// One chunk of node u's arcs from a (one arc per thread): the admissible
+// residual c of this thread's arc.
+__device__ __forceinline__ unsigned long long admissible(const PR& P, uint64_t a, uint64_t end,
+                                                         uint32_t hu, uint32_t* v) {
+    unsigned long long c = 0;
+    *v = 0;
+    if (a < end) {
+        *v = P.to[a];
+        unsigned long long ca = P.cf[a];
+        if (ca > 0 && P.height[*v] + 1 == hu) c = ca;
+    }
+    return c;
 }
 
-// Warp per active node u.
-__global__ void k_push(const uint32_t* list, const uint32_t* nlist, const uint64_t* head,
-                       const uint32_t* to, const uint64_t* rev, unsigned long long* cf,
-                       unsigned long long* excess, const uint32_t* height) {
+__device__ __forceinline__ void push_arc(const PR& P, uint64_t a, uint32_t v,
+                                         unsigned long long d) {
+    atomicAdd(&P.cf[a], (unsigned long long)(-(long long)d));
+    atomicAdd(&P.cf[P.rev[a]], d);
+    atomicAdd(&P.excess[v], d);
+}
+
+// Warp per small active node.  The prefix of the admissible residuals is
+// saturating: a saturated sum leaves the exclusive prefix above any excess
+// (residuals < 2^63, excess < 2^61), so no push is made from it.
+__global__ void k_push_small(PR P, const uint32_t* list, const uint32_t* c) {
     uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned lane = lane_id();
-    const uint32_t n = *nlist;
+    const uint32_t n = c[0];
     for (uint64_t i = gw; i < n; i += nw) {
-        uint32_t u = list[i];
-        const unsigned long long e0 = excess[u];
-        const uint32_t hu = height[u];
+        const uint32_t u = list[i];
+        const unsigned long long e0 = P.excess[u];
+        const uint32_t hu = P.height[u];
+        const uint64_t end = P.head[u + 1];
         unsigned long long rem = e0;
-        for (uint64_t p0 = head[u]; p0 < head[u + 1] && rem > 0; p0 += 32) {
-            uint64_t a = p0 + lane;
-            unsigned long long c = 0;
-            uint32_t v = 0;
-            if (a < head[u + 1]) {
-                v = to[a];
-                unsigned long long ca = cf[a];
-                if (ca > 0 && height[v] + 1 == hu) c = ca;
-            }
-            // inclusive prefix of c over the lanes (saturating)
-            unsigned long long incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)lane >= o) incl = sat_add(incl, y);
-            }
-            // exact unless saturated, and a saturated sum leaves excl far
-            // above any excess (capacities < 2^63, excess < 2^61)
-            unsigned long long excl = incl - c;
+        uint64_t p0 = P.cur[u], ncur = end;
+        while (p0 < end && rem > 0) {
+            uint32_t v;
+            const uint64_t a = p0 + lane;
+            unsigned long long cv = admissible(P, a, end, hu, &v);
+            unsigned long long incl = warp_scan_sat(cv), excl = incl - cv;
             unsigned long long d = 0;
-            if (c > 0 && excl < rem) d = c < rem - excl ? c : rem - excl;
-            if (d) {
-                atomicAdd(&cf[a], (unsigned long long)(-(long long)d));
-                atomicAdd(&cf[rev[a]], d);
-                atomicAdd(&excess[v], d);
-            }
-            unsigned long long tot = warp_sum(d);
-            rem -= tot;
+            if (cv > 0 && excl < rem) d = cv < rem - excl ? cv : rem - excl;
+            if (d) push_arc(P, a, v, d);
+            // first arc with admissible residual left: the new current arc
+            uint64_t left = cv > d ? a : ~0ull;
+            left = warp_min_u64(left);
+            if (left < ncur) ncur = left;
+            unsigned long long tot = __shfl_sync(0xffffffffu, incl, 31);
+            rem -= tot < rem ? tot : rem;
+            p0 += 32;
         }
-        if (lane == 0 && rem != e0) atomicAdd(&excess[u], (unsigned long long)(-(long long)(e0 - rem)));
+        if (lane == 0) {
+            P.cur[u] = ncur < p0 ? ncur : (p0 < end ? p0 : end);
+            if (rem != e0) atomicAdd(&P.excess[u], (unsigned long long)(-(long long)(e0 - rem)));
+        }
     }
 }
 
-// Warp per active node: new height (into nh[i]) for nodes still holding
-// excess, from the heights of the round's start.
-__global__ void k_relabel(const uint32_t* list, const uint32_t* nlist, uint64_t N,
-                          const uint64_t* head, const uint32_t* to,
-                          const unsigned long long* cf, const unsigned long long* excess,
-                          const uint32_t* height, uint32_t* nh) {
+// Block per big active node (kBigThreads threads).
+__global__ void __launch_bounds__(kBigThreads) k_push_big(PR P, const uint32_t* list,
+                                                          const uint32_t* c) {
+    constexpr int NW = kBigThreads / 32;
+    __shared__ unsigned long long s_w[NW];
+    __shared__ unsigned long long s_cur;
+    const unsigned lane = lane_id(), warp = warp_id();
+    const uint32_t n = c[1];
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t u = list[i];
+        const unsigned long long e0 = P.excess[u];
+        const uint32_t hu = P.height[u];
+        const uint64_t end = P.head[u + 1];
+        unsigned long long rem = e0;
+        uint64_t p0 = P.cur[u];
+        if (threadIdx.x == 0) s_cur = end;
+        __syncthreads();
+        while (p0 < end && rem > 0) {
+            uint32_t v;
+            const uint64_t a = p0 + threadIdx.x;
+            unsigned long long cv = admissible(P, a, end, hu, &v);
+            unsigned long long incl = warp_scan_sat(cv);
+            if (lane == 31) s_w[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long t = lane < NW ? s_w[lane] : 0;
+                t = warp_scan_sat(t);
+                if (lane < NW) s_w[lane] = t;
+            }
+            __syncthreads();
+            if (warp > 0) incl = sat_add(incl, s_w[warp - 1]);
+            const unsigned long long tot = s_w[NW - 1];
+            unsigned long long excl = incl - cv;
+            unsigned long long d = 0;
+            if (cv > 0 && excl < rem) d = cv < rem - excl ? cv : rem - excl;
+            if (d) push_arc(P, a, v, d);
+            if (cv > d) atomicMin(&s_cur, (unsigned long long)a);
+            rem -= tot < rem ? tot : rem;
+            p0 += kBigThreads;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            uint64_t nc = s_cur;
+            P.cur[u] = nc < p0 ? nc : (p0 < end ? p0 : end);
+            if (rem != e0) atomicAdd(&P.excess[u], (unsigned long long)(-(long long)(e0 - rem)));
+        }
+        __syncthreads();
+    }
+}
+
+// New height of a node that holds excess with its current arc at the end:
+// 1 + the least height over its residual arcs (N if none), else kUnset.
+__global__ void k_relabel_small(PR P, const uint32_t* list, const uint32_t* c, uint32_t* nh) {
     uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned lane = lane_id();
-    const uint32_t n = *nlist;
+    const uint32_t n = c[0];
     for (uint64_t i = gw; i < n; i += nw) {
-        uint32_t u = list[i];
-        uint32_t hu = height[u];
-        if (excess[u] == 0) {
-            if (lane == 0) nh[i] = hu;
+        const uint32_t u = list[i];
+        const uint64_t end = P.head[u + 1];
+        if (P.excess[u] == 0 || P.cur[u] < end) {
+            if (lane == 0) nh[i] = kUnset;
             continue;
         }
         uint32_t m = kUnset;
-        for (uint64_t a = head[u] + lane; a < head[u + 1]; a += 32)
-            if (cf[a] > 0) {
-                uint32_t hv = height[to[a]];
+        for (uint64_t a = P.head[u] + lane; a < end; a += 32)
+            if (P.cf[a] > 0) {
+                uint32_t hv = P.height[P.to[a]];
                 m = hv < m ? hv : m;
             }
         for (int o = 16; o > 0; o >>= 1) {
@@ -519,20 +661,60 @@ __global__ void k_relabel(const uint32_t* list, const uint32_t* nlist, uint64_t 
             m = y < m ? y : m;
         }
         if (lane == 0) {
-            uint64_t nv = m == kUnset ? N : (uint64_t)m + 1;
-            if (nv > N) nv = N;
-            if (nv < hu) nv = hu;
+            uint64_t nv = m == kUnset ? P.N : (uint64_t)m + 1;
+            if (nv > P.N) nv = P.N;
             nh[i] = (uint32_t)nv;
         }
     }
 }
 
-__global__ void k_apply(const uint32_t* list, const uint32_t* nlist, const uint32_t* nh,
-                        uint32_t* height) {
-    const uint32_t n = *nlist;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        height[list[i]] = nh[i];
+__global__ void __launch_bounds__(kBigThreads) k_relabel_big(PR P, const uint32_t* list,
+                                                             const uint32_t* c, uint32_t* nh) {
+    __shared__ uint32_t s_m;
+    const uint32_t n = c[1];
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t u = list[i];
+        const uint64_t end = P.head[u + 1];
+        if (P.excess[u] == 0 || P.cur[u] < end) {
+            if (threadIdx.x == 0) nh[i] = kUnset;
+            continue;
+        }
+        if (threadIdx.x == 0) s_m = kUnset;
+        __syncthreads();
+        uint32_t m = kUnset;
+        for (uint64_t a = P.head[u] + threadIdx.x; a < end; a += blockDim.x)
+            if (P.cf[a] > 0) {
+                uint32_t hv = P.height[P.to[a]];
+                m = hv < m ? hv : m;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+            m = y < m ? y : m;
+        }
+        if (lane_id() == 0 && m != kUnset) atomicMin(&s_m, m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t nv = s_m == kUnset ? P.N : (uint64_t)s_m + 1;
+            if (nv > P.N) nv = P.N;
+            nh[i] = (uint32_t)nv;
+        }
+        __syncthreads();
+    }
+}
+
+// Relabelled nodes take their new height and restart at their first arc.
+__global__ void k_apply(PR P, const uint32_t* ls, const uint32_t* lb, const uint32_t* c,
+                        const uint32_t* nhs, const uint32_t* nhb) {
+    const uint64_t ns = c[0], nb = c[1];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns + nb;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = i < ns ? ls[i] : lb[i - ns];
+        uint32_t v = i < ns ? nhs[i] : nhb[i - ns];
+        if (v != kUnset) {
+            P.height[u] = v;
+            P.cur[u] = P.head[u];
+        }
+    }
 }
 
 // Vertex v of the core is on the source side when it cannot reach t.
@@ -722,30 +904,71 @@ struct CutStats {
     uint64_t rounds = 0, relabels = 0;
 };
 
-// Backward breadth-first search from t: exact residual distances to t,
-// N for nodes that cannot reach it (and for s).
-dsd_status global_relabel(const Net& net, cudaStream_t s, uint32_t* height, uint32_t* fa,
-                          uint32_t* fb, uint32_t* ctr) {
-    k_bfs_init<<<grid_for_n(net.N), 256, 0, s>>>(net.N, height, fa, ctr); note_launch();
-    uint32_t nf = 1, d = 0;
-    while (nf) {
-        DSD_CU(cudaMemsetAsync(ctr + 1, 0, 4, s));
-        k_bfs_step<<<grid_for_warps(nf), 256, 0, s>>>(fa, ctr, fb, ctr + 1, d, net.head, net.to,
-                                                      net.rev, net.cf, height);
+// Device buffers of one minimum cut.
+struct CutWork {
+    unsigned long long* excess = nullptr;
+    uint32_t* height = nullptr;
+    uint64_t* cur = nullptr;
+    uint32_t* ls = nullptr;       // active lists: small, big
+    uint32_t* lb = nullptr;
+    uint32_t* nhs = nullptr;      // new heights for them
+    uint32_t* nhb = nullptr;
+    uint32_t* f[4] = {};          // frontiers: small/big, two levels
+    uint32_t* ctr = nullptr;      // [0,1] active, [2..5] frontier counters
+    unsigned long long* cnt = nullptr;
+};
+
+dsd_status cut_alloc(CutWork* w, uint64_t N, cudaStream_t s) {
+    DSD_TRY(dalloc(&w->excess, N + 1, s));
+    DSD_TRY(dalloc(&w->height, N + 1, s));
+    DSD_TRY(dalloc(&w->cur, N + 1, s));
+    DSD_TRY(dalloc(&w->ls, N + 1, s));
+    DSD_TRY(dalloc(&w->lb, N + 1, s));
+    DSD_TRY(dalloc(&w->nhs, N + 1, s));
+    DSD_TRY(dalloc(&w->nhb, N + 1, s));
+    for (auto& f : w->f) DSD_TRY(dalloc(&f, N + 1, s));
+    DSD_TRY(dalloc(&w->ctr, 8, s));
+    DSD_TRY(dalloc(&w->cnt, 1, s));
+    return DSD_OK;
+}
+
+void cut_free(CutWork* w, cudaStream_t s) {
+    void* ptrs[] = {w->excess, w->height, w->cur, w->ls, w->lb, w->nhs, w->nhb,
+                    w->f[0], w->f[1], w->f[2], w->f[3], w->ctr, w->cnt};
+    for (void* p : ptrs) dev_free(p, s);
+    *w = CutWork();
+}
+
+constexpr unsigned kSmallGrid = 152 * 8;   // blocks of 256 threads (warp per node)
+constexpr unsigned kBigGrid = 152 * 4;     // blocks of kBigThreads (block per node)
+
+// Backward breadth-first search from t: exact residual distances to t, N for
+// nodes that cannot reach it (and for s); resets the current arcs.
+dsd_status global_relabel(const PR& P, CutWork& w, cudaStream_t s) {
+    uint32_t *fs = w.f[0], *fb = w.f[1], *os = w.f[2], *ob = w.f[3];
+    uint32_t* cin = w.ctr + 2;
+    uint32_t* cout = w.ctr + 4;
+    k_bfs_init<<<grid_for_n(P.N), 256, 0, s>>>(P, fs, fb, cin); note_launch();
+    for (uint32_t d = 0;; d++) {
+        uint32_t nc[2] = {0, 0};
+        DSD_CU(cudaMemsetAsync(cout, 0, 8, s));
+        k_bfs_small<<<kSmallGrid, 256, 0, s>>>(P, fs, cin, d, os, ob, cout);
+        k_bfs_big<<<kBigGrid, kBigThreads, 0, s>>>(P, fb, cin, d, os, ob, cout);
         note_launch();
-        DSD_CU(cudaMemcpyAsync(ctr, ctr + 1, 4, cudaMemcpyDeviceToDevice, s));
-        DSD_CU(cudaMemcpyAsync(&nf, ctr + 1, 4, cudaMemcpyDeviceToHost, s));
+        note_launch();
+        DSD_CU(cudaMemcpyAsync(nc, cout, 8, cudaMemcpyDeviceToHost, s));
         DSD_CU(cudaStreamSynchronize(s));
-        uint32_t* t = fa;
-        fa = fb;
-        fb = t;
-        d++;
-        if (d > net.N) {
+        if (nc[0] + nc[1] == 0) break;
+        if (d > P.N) {
             set_error("breadth-first search did not settle");
             return DSD_ERR_INTERNAL;
         }
+        uint32_t* t;
+        t = fs; fs = os; os = t;
+        t = fb; fb = ob; ob = t;
+        t = cin; cin = cout; cout = t;
     }
-    k_bfs_finish<<<grid_for_n(net.N), 256, 0, s>>>(net.N, height); note_launch();
+    k_bfs_finish<<<grid_for_n(P.N), 256, 0, s>>>(P); note_launch();
     DSD_LAUNCHED();
     return DSD_OK;
 }
@@ -757,53 +980,55 @@ dsd_status min_cut(const Net& net, int h, uint64_t p, uint64_t q, cudaStream_t s
                    unsigned long long* flow, uint32_t* inA, uint64_t* sizeA, CutStats* cs) {
     dsd_status st = DSD_OK;
     const uint64_t N = net.N;
-    unsigned long long* excess = nullptr;
-    uint32_t *height = nullptr, *list = nullptr, *nh = nullptr, *fa = nullptr, *fb = nullptr,
-             *ctr = nullptr;
-    unsigned long long* cnt = nullptr;
+    CutWork w;
+    PR P;
     const uint64_t t0 = now_ns();
     const uint64_t limit_rounds = 4 * N + 100000;
     const int kRoundsPerRelabel = 8;
-    XSTEP(dalloc(&excess, N + 1, s));
-    XSTEP(dalloc(&height, N + 1, s));
-    XSTEP(dalloc(&list, N + 1, s));
-    XSTEP(dalloc(&nh, N + 1, s));
-    XSTEP(dalloc(&fa, N + 1, s));
-    XSTEP(dalloc(&fb, N + 1, s));
-    XSTEP(dalloc(&ctr, 4, s));
-    XSTEP(dalloc(&cnt, 1, s));
+    XSTEP(cut_alloc(&w, N, s));
+    P.head = net.head;
+    P.to = net.to;
+    P.rev = net.rev;
+    P.kind = net.kind;
+    P.cf = net.cf;
+    P.excess = w.excess;
+    P.height = w.height;
+    P.cur = w.cur;
+    P.vdeg = net.vdeg;
+    P.p = p;
+    P.q = q;
+    P.h = h;
+    P.N = N;
     k_caps<<<grid_for_n(net.E), 256, 0, s>>>(net.E, net.kind, net.to, net.vdeg, p, q, h, net.cf);
     note_launch();
-    XCU(cudaMemsetAsync(excess, 0, (N + 1) * 8, s));
-    k_preflow<<<grid_for_n(net.nW), 256, 0, s>>>(net.nW, net.head, net.rev, net.cf, excess);
+    XCU(cudaMemsetAsync(w.excess, 0, (N + 1) * 8, s));
+    k_preflow<<<grid_for_n(net.nW), 256, 0, s>>>(net.nW, net.head, net.rev, net.cf, w.excess);
     note_launch();
-    XSTEP(global_relabel(net, s, height, fa, fb, ctr));
+    XSTEP(global_relabel(P, w, s));
     cs->relabels++;
     for (;;) {
-        uint32_t nact = 0;
-        XCU(cudaMemsetAsync(ctr + 2, 0, 4, s));
-        k_collect<<<grid_for_n(N), 256, 0, s>>>(N, excess, height, list, ctr + 2); note_launch();
-        XSTEP(read_back(&nact, ctr + 2, s));
-        if (nact == 0) break;
+        uint32_t na[2] = {0, 0};
+        XCU(cudaMemsetAsync(w.ctr, 0, 8, s));
+        k_collect<<<grid_for_n(N), 256, 0, s>>>(P, w.ls, w.lb, w.ctr); note_launch();
+        XCU(cudaMemcpyAsync(na, w.ctr, 8, cudaMemcpyDeviceToHost, s));
+        XCU(cudaStreamSynchronize(s));
+        if (na[0] + na[1] == 0) break;
         for (int it = 0; it < kRoundsPerRelabel; it++) {
             if (it) {
-                XCU(cudaMemsetAsync(ctr + 2, 0, 4, s));
-                k_collect<<<grid_for_n(N), 256, 0, s>>>(N, excess, height, list, ctr + 2);
+                XCU(cudaMemsetAsync(w.ctr, 0, 8, s));
+                k_collect<<<grid_for_n(N), 256, 0, s>>>(P, w.ls, w.lb, w.ctr);
                 note_launch();
             }
-            const unsigned gw = grid_for_warps(nact);
-            k_push<<<gw, 256, 0, s>>>(list, ctr + 2, net.head, net.to, net.rev, net.cf, excess,
-                                      height);
-            k_relabel<<<gw, 256, 0, s>>>(list, ctr + 2, N, net.head, net.to, net.cf, excess,
-                                         height, nh);
-            k_apply<<<grid_for_n(nact), 256, 0, s>>>(list, ctr + 2, nh, height);
-            note_launch();
-            note_launch();
-            note_launch();
+            k_push_small<<<kSmallGrid, 256, 0, s>>>(P, w.ls, w.ctr);
+            k_push_big<<<kBigGrid, kBigThreads, 0, s>>>(P, w.lb, w.ctr);
+            k_relabel_small<<<kSmallGrid, 256, 0, s>>>(P, w.ls, w.ctr, w.nhs);
+            k_relabel_big<<<kBigGrid, kBigThreads, 0, s>>>(P, w.lb, w.ctr, w.nhb);
+            k_apply<<<kSmallGrid, 256, 0, s>>>(P, w.ls, w.lb, w.ctr, w.nhs, w.nhb);
+            for (int k = 0; k < 5; k++) note_launch();
             cs->rounds++;
         }
         XCU(cudaGetLastError());
-        XSTEP(global_relabel(net, s, height, fa, fb, ctr));
+        XSTEP(global_relabel(P, w, s));
         cs->relabels++;
         if (cs->rounds > limit_rounds || now_ns() - t0 > wait_limit_ns()) {
             set_error("push-relabel did not finish within %llu rounds / the wait limit",
@@ -812,22 +1037,19 @@ dsd_status min_cut(const Net& net, int h, uint64_t p, uint64_t q, cudaStream_t s
             goto done;
         }
     }
-    XSTEP(read_back(flow, excess + 1, s));
-    XCU(cudaMemsetAsync(cnt, 0, 8, s));
+    XSTEP(read_back(flow, w.excess + 1, s));
+    XCU(cudaMemsetAsync(w.cnt, 0, 8, s));
     if (net.nW) {
-        k_source_side<<<grid_for_n(net.nW), 256, 0, s>>>(net.nW, height, N, inA, cnt);
+        k_source_side<<<grid_for_n(net.nW), 256, 0, s>>>(net.nW, w.height, N, inA, w.cnt);
         note_launch();
     }
     {
         unsigned long long a = 0;
-        XSTEP(read_back(&a, cnt, s));
+        XSTEP(read_back(&a, w.cnt, s));
         *sizeA = a;
     }
 done:
-    {
-        void* ptrs[] = {excess, height, list, nh, fa, fb, ctr, cnt};
-        for (void* ptr : ptrs) dev_free(ptr, s);
-    }
+    cut_free(&w, s);
     return st;
 }
 
@@ -960,6 +1182,7 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
     }
     dsd_exact_info I;
     memset(&I, 0, sizeof(I));
+    uint64_t tm = now_ns();
     dsd_core_app_result app;
     DSD_TRY(dsd_core_app(g, h, nullptr, nullptr, DSD_MEM_HOST, &app));
     cudaStream_t s = g->stream;
@@ -999,6 +1222,7 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
         I.k2 = ceil_div(p, q);
         I.lower_mu = p;
         I.lower_size = (uint32_t)q;
+        I.locate_ns = now_ns() - tm;
         // Dinkelbach's iteration on the located core
         for (;;) {
             uint64_t gq = gcd_u64(p, q);
@@ -1015,9 +1239,11 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
                 orig = nullptr;
                 dev_free(inA, s);
                 inA = nullptr;
+                tm = now_ns();
                 XSTEP(located_core(g, core, k, &W, &orig));
                 XSTEP(build_network(W, h, &net));
                 XSTEP(dalloc(&inA, (size_t)W->n + 1, s));
+                I.build_ns += now_ns() - tm;
                 kcur = k;
                 if (I.cuts == 0) {
                     I.net_nodes = (uint32_t)net.N;
@@ -1034,7 +1260,9 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
             }
             unsigned long long F = 0;
             CutStats cs;
+            tm = now_ns();
             XSTEP(min_cut(net, h, p, q, s, &F, inA, &sizeA, &cs));
+            I.cut_ns += now_ns() - tm;
             I.cuts++;
             I.rounds += cs.rounds;
             I.relabels += cs.relabels;
@@ -1062,6 +1290,7 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
             }
             break;
         }
+        tm = now_ns();
         XCU(cudaMemsetAsync(flag, 0, ((size_t)n + 1) * 4, s));
         k_mark_g<<<grid_for_n(W->n), 256, 0, s>>>(W->n, inA, W->old_of, orig, flag);
         note_launch();
@@ -1088,6 +1317,7 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
         if (tmp) XCU(cudaMemcpyAsync(cds, tmp, (size_t)I.size * 4, cudaMemcpyDeviceToHost, s));
     }
     XCU(cudaStreamSynchronize(s));
+    I.verify_ns = now_ns() - tm;
     *info = I;
 done:
     net_free(&net, s);
