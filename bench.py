@@ -19,7 +19,10 @@ more objects on the same line (rank 0, skipped with --no-learned /
              acceptance rate, identical outputs; beside it CoreApp's own
              top-down schedule (dsd_core_app_topdown) on the same graph;
   batched -- 4096 mixed graphs (h in {2,3,4}) in one CUDA-graph replay of the
-             persistent batch kernel vs a host loop of the plain path.
+             persistent batch kernel vs a host loop of the plain path;
+  exact   -- CoreExact (dsd_core_exact) on the step's graph with its
+             decomposition cached: device time of the exact stage, rho_opt
+             against the densest level's density, the flow network's size.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -60,6 +63,11 @@ def parse(argv=None):
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched leg (4096 mixed graphs)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-exact", action="store_true",
+                    help="skip the CoreExact leg")
+    ap.add_argument("--exact-only", action="store_true",
+                    help="run only the CoreExact leg and print it (a short command for "
+                         "kernel profiles)")
     ap.add_argument("--once", action="store_true",
                     help="build the workload graph, run dsd_core_app once, print k_max and "
                          "exit (a short command for kernel profiles)")
@@ -520,6 +528,58 @@ def run_reference(args, rank, world):
     }
 
 
+# ------------------------------------------------------------ CoreExact
+
+def run_exact(args, local):
+    """dsd_core_exact on the workload graph, the decomposition already cached
+    on the handle: device time per call over --steps calls after --warmup."""
+    import torch
+    from fractions import Fraction
+    from paper_1906_00341_gb300 import graphgen as gg
+    from paper_1906_00341_gb300 import _lib as L
+    L.load()
+    dev = torch.device("cuda", local)
+    n, s, d, _ = gg.workload(args.workload)
+    h = args.h
+    src = torch.from_numpy(s.astype(np.int32)).to(dev)
+    dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE, sp)
+    app = L.dsd_core_app(g, h, 0, 0, L.DSD_MEM_HOST)
+    cds = torch.empty(n, dtype=torch.int32, device=dev)
+    info = None
+    for _ in range(max(args.warmup, 1)):
+        info = L.dsd_core_exact(g, h, cds.data_ptr(), L.DSD_MEM_DEVICE)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = L.dsd_core_exact(g, h, cds.data_ptr(), L.DSD_MEM_DEVICE)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    L.dsd_graph_destroy(g)
+    rho = Fraction(int(info.mu), int(info.size)) if info.size else Fraction(0)
+    rho_s = Fraction(int(app.densest_mu), int(app.densest_size)) if app.densest_size else Fraction(0)
+    return {
+        "call": "dsd_core_exact (decomposition cached on the handle)",
+        "workload": args.workload, "h": h,
+        "ms": float(np.median(times)), "ms_all": [round(t, 3) for t in times],
+        "rho_opt": [int(info.mu), int(info.size)], "rho_opt_float": float(rho),
+        "densest_level": [int(app.densest_mu), int(app.densest_size)],
+        "densest_level_over_opt": float(rho_s / rho) if rho else None,
+        "cuts": int(info.cuts), "k1": int(info.k1), "k2": int(info.k2),
+        "components": int(info.components), "net_nodes": int(info.net_nodes),
+        "net_arcs": int(info.net_arcs), "rounds": int(info.rounds),
+        "relabels": int(info.relabels),
+        "phase_ms": {"locate": info.locate_ns / 1e6, "build": info.build_ns / 1e6,
+                     "cut": info.cut_ns / 1e6, "verify": info.verify_ns / 1e6},
+    }
+
+
 def run_once(args, local):
     import torch
     from paper_1906_00341_gb300 import graphgen as gg
@@ -545,6 +605,10 @@ def main():
         if rank == 0:
             run_once(args, local)
         return 0
+    if args.exact_only:
+        if rank == 0:
+            print(json.dumps(run_exact(args, local)), flush=True)
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0
@@ -562,6 +626,8 @@ def main():
             line["learned"] = run_learned(args, local)
         if graphs is not None:
             line["batched"] = run_batched(args, local, graphs)
+        if not args.no_exact:
+            line["exact"] = run_exact(args, local)
         if not args.no_cpu_baseline and world == 1:
             ns, ss, ds = cpu_sample(n, s, d)
             t, smu, _ = time_oracle(ns, ss, ds, h)

@@ -74,6 +74,10 @@ def _load():
     lib.orc_exact_cds.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u8p, _u64p,
                                   _u64p, _u32p]
     lib.orc_exact_cds.restype = ctypes.c_int
+    lib.orc_densest_check.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_uint64, _u8p,
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.orc_densest_check.restype = ctypes.c_int
     for f in ("orc_pattern_degrees", "orc_pattern_core_decompose", "orc_pattern_level_stats"):
         getattr(lib, f).restype = ctypes.c_int
     for f in ("orc_clique_degrees", "orc_vertex_clique_degree", "orc_vertex_clique_degrees",
@@ -244,6 +248,21 @@ def exact_cds(g: Graph, h: int):
                              _p(mu, _u64p), _p(size, _u64p), _p(steps, _u32p)))
     cds = np.flatnonzero(mark[:g.n]).astype(np.uint32)
     return dict(cds=cds, mu=int(mu[0]), size=int(size[0]), steps=int(steps[0]))
+
+
+def densest_check(g: Graph, h: int, p: int, q: int):
+    """One minimum cut of Algorithm 1's network at alpha = p/q.
+
+    Returns (beats, largest_source_side): beats is True when some vertex set
+    has density above p/q; at p/q = rho_opt it is False and the set is the
+    largest densest set (sorted ids).
+    """
+    lib = _load()
+    mark = np.zeros(max(g.n, 1), np.uint8)
+    beats = ctypes.c_int(0)
+    _check(lib.orc_densest_check(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), h, int(p), int(q),
+                                 _p(mark, _u8p), ctypes.byref(beats)))
+    return bool(beats.value), np.flatnonzero(mark[:g.n]).astype(np.uint32)
 
 
 # ------------------------------------------------------------ patterns (Sec. 6)

@@ -966,6 +966,54 @@ static u128 gcd128(u128 a, u128 b) {
     return a;
 }
 
+/* Algorithm 1's network for G (working graph g, mu(G) = mu): s, t, one node
+ * per vertex and per (h-1)-clique psi (listed once each); arcs s -> v, v -> t,
+ * psi -> v for v in psi, w -> psi for every w adjacent to all of psi. */
+static int alg1_network(const wgraph* g, int h, uint64_t mu, fnet* F) {
+    const uint32_t n = g->n;
+    int rc = ORC_ENOMEM;
+    lister C;
+    memset(&C, 0, sizeof(C));
+    uint32_t* cn = (uint32_t*)malloc(((size_t)g->maxdeg + 1) * sizeof(uint32_t));
+    uint32_t* cn2 = (uint32_t*)malloc(((size_t)g->maxdeg + 1) * sizeof(uint32_t));
+    if (!cn || !cn2) goto out;
+    /* Lambda: the (h-1)-cliques, each once */
+    if (lister_init(&C, g, h - 1, visit_store)) goto out;
+    list_all(&C);
+    if (C.overflow) goto out;
+    uint64_t nl = C.nstore;
+    if ((uint64_t)n + nl + 2 >= ((uint64_t)1 << 31)) { rc = ORC_EINVAL; goto out; }
+    uint32_t N = (uint32_t)(2 + n + nl);
+    uint64_t E = 2 * (2 * (uint64_t)n + (uint64_t)(h - 1) * nl + (uint64_t)h * mu);
+    if (fn_init(F, N, E)) goto out;
+    for (uint32_t v = 0; v < n; v++) {
+        fn_arc(F, 0, 2 + v, ARC_S);
+        fn_arc(F, 2 + v, 1, ARC_T);
+    }
+    for (uint64_t i = 0; i < nl; i++) {
+        const uint32_t* psi = C.store + i * (h - 1);
+        uint32_t node = (uint32_t)(2 + n + i);
+        for (int j = 0; j < h - 1; j++) fn_arc(F, node, 2 + psi[j], ARC_INF);
+        /* common neighbours of psi's members: psi + w is an h-clique */
+        uint32_t x0 = psi[0];
+        uint32_t k = (uint32_t)(g->off[x0 + 1] - g->off[x0]);
+        memcpy(cn, g->adj + g->off[x0], (size_t)k * sizeof(uint32_t));
+        for (int j = 1; j < h - 1 && k; j++) {
+            uint32_t x = psi[j];
+            k = intersect(cn, k, g->adj + g->off[x], g->off[x + 1] - g->off[x], cn2);
+            memcpy(cn, cn2, (size_t)k * sizeof(uint32_t));
+        }
+        for (uint32_t j = 0; j < k; j++) fn_arc(F, 2 + cn[j], node, ARC_Q);
+    }
+    rc = F->E == E ? ORC_OK : -3;
+out:
+    free(C.store);
+    lister_free(&C);
+    free(cn); free(cn2);
+    if (rc) fn_free(F);
+    return rc;
+}
+
 /* The CDS of G (Problem 1) by Algorithm 1, and then the largest densest set.
  *
  * in_cds[v] (original ids) marks the union of all vertex sets of maximum
@@ -983,17 +1031,14 @@ int orc_exact_cds(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
     wgraph g;
     if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
     int rc = ORC_ENOMEM;
-    lister L, C;
+    lister L;
     memset(&L, 0, sizeof(L));
-    memset(&C, 0, sizeof(C));
     fnet F;
     memset(&F, 0, sizeof(F));
     uint64_t* deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
     uint8_t* inD = (uint8_t*)calloc((size_t)(n ? n : 1), 1);
     uint8_t* mark = NULL;
-    uint32_t* cn = (uint32_t*)malloc(((size_t)g.maxdeg + 1) * sizeof(uint32_t));
-    uint32_t* cn2 = (uint32_t*)malloc(((size_t)g.maxdeg + 1) * sizeof(uint32_t));
-    if (!deg || !inD || !cn || !cn2) goto out;
+    if (!deg || !inD) goto out;
     /* clique-degrees and mu(G) */
     if (lister_init(&L, &g, h, visit_count)) goto out;
     L.deg = deg;
@@ -1010,37 +1055,11 @@ int orc_exact_cds(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
     for (uint32_t v = 0; v < n; v++) if (deg[v] > maxdeg) maxdeg = deg[v];
     u128 nn1 = (u128)n * (n - 1);
     if (nn1 * maxdeg >= ((u128)1 << 60)) { rc = ORC_EINVAL; goto out; }
-    /* Lambda: the (h-1)-cliques, each once */
-    if (lister_init(&C, &g, h - 1, visit_store)) goto out;
-    list_all(&C);
-    if (C.overflow) goto out;
-    uint64_t nl = C.nstore;
-    if ((uint64_t)n + nl + 2 >= ((uint64_t)1 << 31)) { rc = ORC_EINVAL; goto out; }
-    uint32_t N = (uint32_t)(2 + n + nl);
-    uint64_t E = 2 * (2 * (uint64_t)n + (uint64_t)(h - 1) * nl + (uint64_t)h * mu);
-    if (fn_init(&F, N, E)) goto out;
-    mark = (uint8_t*)malloc(N);
+    rc = alg1_network(&g, h, mu, &F);
+    if (rc) goto out;
+    rc = ORC_ENOMEM;
+    mark = (uint8_t*)malloc(F.N);
     if (!mark) goto out;
-    for (uint32_t v = 0; v < n; v++) {
-        fn_arc(&F, 0, 2 + v, ARC_S);
-        fn_arc(&F, 2 + v, 1, ARC_T);
-    }
-    for (uint64_t i = 0; i < nl; i++) {
-        const uint32_t* psi = C.store + i * (h - 1);
-        uint32_t node = (uint32_t)(2 + n + i);
-        for (int j = 0; j < h - 1; j++) fn_arc(&F, node, 2 + psi[j], ARC_INF);
-        /* common neighbours of psi's members: psi + w is an h-clique */
-        uint32_t x0 = psi[0];
-        uint32_t k = (uint32_t)(g.off[x0 + 1] - g.off[x0]);
-        memcpy(cn, g.adj + g.off[x0], (size_t)k * sizeof(uint32_t));
-        for (int j = 1; j < h - 1 && k; j++) {
-            uint32_t x = psi[j];
-            k = intersect(cn, k, g.adj + g.off[x], g.off[x + 1] - g.off[x], cn2);
-            memcpy(cn, cn2, (size_t)k * sizeof(uint32_t));
-        }
-        for (uint32_t j = 0; j < k; j++) fn_arc(&F, 2 + cn[j], node, ARC_Q);
-    }
-    if (F.E != E) { rc = -3; goto out; }
     /* binary search (l, u) = (L, U) / 2^t over [0, max deg] */
     u128 Lo = 0, Up = maxdeg;
     int t = 0, haveD = 0;
@@ -1088,10 +1107,49 @@ int orc_exact_cds(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
     rc = ORC_OK;
 out:
     fn_free(&F);
-    free(C.store);
-    lister_free(&C);
     lister_free(&L);
-    free(deg); free(inD); free(mark); free(cn); free(cn2);
+    free(deg); free(inD); free(mark);
+    wg_free(&g);
+    return rc;
+}
+
+/* One minimum cut of Algorithm 1's network at alpha = p / q (q > 0): a
+ * certificate check of a claimed optimum.  *beats = 1 when some vertex set A
+ * has mu(A) > alpha |A| (the cut is below q h mu(G)); in_set (original ids)
+ * marks the vertices of the largest source side of a minimum cut.  At
+ * alpha = rho_opt, *beats = 0 and in_set is the largest densest set. */
+int orc_densest_check(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
+                      uint64_t p, uint64_t q, uint8_t* in_set, int* beats) {
+    if (check_h(h) || q == 0) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    int rc = ORC_ENOMEM;
+    lister L;
+    memset(&L, 0, sizeof(L));
+    fnet F;
+    memset(&F, 0, sizeof(F));
+    uint8_t* mark = NULL;
+    uint64_t* deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    if (!deg) goto out;
+    if (lister_init(&L, &g, h, visit_count)) goto out;
+    L.deg = deg;
+    list_all(&L);
+    rc = alg1_network(&g, h, L.mu, &F);
+    if (rc) goto out;
+    rc = ORC_ENOMEM;
+    mark = (uint8_t*)malloc(F.N);
+    if (!mark) goto out;
+    fn_capacities(&F, deg, h, p, q);
+    u128 flow;
+    if (fn_maxflow(&F, &flow)) goto out;
+    *beats = flow < (u128)q * h * L.mu;
+    fn_reach_t(&F, mark);
+    for (uint32_t i = 0; i < n; i++) in_set[g.old_of[i]] = !mark[2 + i];
+    rc = ORC_OK;
+out:
+    fn_free(&F);
+    lister_free(&L);
+    free(deg); free(mark);
     wg_free(&g);
     return rc;
 }

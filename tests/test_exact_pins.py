@@ -71,6 +71,12 @@ def test_exact_bruteforce(orc, h):
         assert np.array_equal(r["cds"], union), (n, h, i, r["cds"], union)
         assert r["size"] == r["cds"].size
         assert r["mu"] == orc.induced_clique_count(g, h, np.isin(np.arange(n), r["cds"]))
+        # one cut as a certificate: nothing beats rho_opt, and just below it
+        # something does
+        beats, side = orc.densest_check(g, h, best.numerator, best.denominator)
+        assert not beats and np.array_equal(side, union)
+        below = best - Fraction(1, 1000 * n * n)
+        assert orc.densest_check(g, h, below.numerator, below.denominator)[0]
 
 
 def test_exact_matches_dinkelbach(orc):
