@@ -781,18 +781,25 @@ enum { ARC_REV = 0, ARC_S = 1, ARC_T = 2, ARC_Q = 3, ARC_INF = 4 };
 typedef struct {
     uint32_t N;               /* 0 = s, 1 = t, 2 + v vertices, then Lambda */
     uint64_t E, cap_e;
-    int64_t* head;
-    int64_t* next;
+    /* arcs as added: e = from -> to, its residual twin e ^ 1 */
+    uint32_t* from;
     uint32_t* to;
     uint8_t* kind;
+    /* the same arcs grouped by tail node (fn_finish): slots first[x] ..
+     * first[x+1]-1 of node x, head node, twin slot, kind, residual capacity */
+    uint64_t* first;
+    uint32_t* head;
+    uint64_t* twin;
+    uint8_t* skind;
     u128* cap;
     int32_t* level;
-    int64_t* it;
+    uint64_t* it;
     uint32_t* queue;
 } fnet;
 
 static void fn_free(fnet* F) {
-    free(F->head); free(F->next); free(F->to); free(F->kind); free(F->cap);
+    free(F->from); free(F->to); free(F->kind);
+    free(F->first); free(F->head); free(F->twin); free(F->skind); free(F->cap);
     free(F->level); free(F->it); free(F->queue);
     memset(F, 0, sizeof(*F));
 }
@@ -801,20 +808,17 @@ static int fn_init(fnet* F, uint32_t N, uint64_t E) {
     memset(F, 0, sizeof(*F));
     F->N = N;
     F->cap_e = E;
-    F->head = (int64_t*)malloc((size_t)N * sizeof(int64_t));
-    F->next = (int64_t*)malloc((size_t)(E ? E : 1) * sizeof(int64_t));
-    F->to = (uint32_t*)malloc((size_t)(E ? E : 1) * sizeof(uint32_t));
-    F->kind = (uint8_t*)malloc((size_t)(E ? E : 1));
-    F->cap = (u128*)malloc((size_t)(E ? E : 1) * sizeof(u128));
+    size_t e1 = (size_t)(E ? E : 1);
+    F->from = (uint32_t*)malloc(e1 * sizeof(uint32_t));
+    F->to = (uint32_t*)malloc(e1 * sizeof(uint32_t));
+    F->kind = (uint8_t*)malloc(e1);
     F->level = (int32_t*)malloc((size_t)N * sizeof(int32_t));
-    F->it = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    F->it = (uint64_t*)malloc((size_t)N * sizeof(uint64_t));
     F->queue = (uint32_t*)malloc((size_t)N * sizeof(uint32_t));
-    if (!F->head || !F->next || !F->to || !F->kind || !F->cap || !F->level || !F->it ||
-        !F->queue) {
+    if (!F->from || !F->to || !F->kind || !F->level || !F->it || !F->queue) {
         fn_free(F);
         return ORC_ENOMEM;
     }
-    for (uint32_t x = 0; x < N; x++) F->head[x] = -1;
     return ORC_OK;
 }
 
@@ -822,27 +826,53 @@ static int fn_init(fnet* F, uint32_t N, uint64_t E) {
 static void fn_arc(fnet* F, uint32_t u, uint32_t v, uint8_t kind) {
     uint64_t e = F->E;
     if (e + 2 > F->cap_e) { F->E = e + 2; return; }   /* counted, caught by the caller */
-    F->to[e] = v; F->kind[e] = kind; F->next[e] = F->head[u]; F->head[u] = (int64_t)e;
-    F->to[e + 1] = u; F->kind[e + 1] = ARC_REV; F->next[e + 1] = F->head[v];
-    F->head[v] = (int64_t)(e + 1);
+    F->from[e] = u; F->to[e] = v; F->kind[e] = kind;
+    F->from[e + 1] = v; F->to[e + 1] = u; F->kind[e + 1] = ARC_REV;
     F->E = e + 2;
 }
 
-/* Capacities for alpha = p / q (all scaled by q). */
+/* Groups the arcs by tail node (a counting sort). */
+static int fn_finish(fnet* F) {
+    size_t e1 = (size_t)(F->E ? F->E : 1);
+    uint64_t* pos = (uint64_t*)malloc(e1 * sizeof(uint64_t));
+    F->first = (uint64_t*)calloc((size_t)F->N + 1, sizeof(uint64_t));
+    F->head = (uint32_t*)malloc(e1 * sizeof(uint32_t));
+    F->twin = (uint64_t*)malloc(e1 * sizeof(uint64_t));
+    F->skind = (uint8_t*)malloc(e1);
+    F->cap = (u128*)malloc(e1 * sizeof(u128));
+    if (!pos || !F->first || !F->head || !F->twin || !F->skind || !F->cap) {
+        free(pos);
+        return ORC_ENOMEM;
+    }
+    for (uint64_t e = 0; e < F->E; e++) F->first[F->from[e] + 1]++;
+    for (uint32_t x = 0; x < F->N; x++) F->first[x + 1] += F->first[x];
+    for (uint64_t e = 0; e < F->E; e++) pos[e] = F->first[F->from[e]]++;
+    for (uint32_t x = F->N; x > 0; x--) F->first[x] = F->first[x - 1];
+    F->first[0] = 0;
+    for (uint64_t e = 0; e < F->E; e++) {
+        F->head[pos[e]] = F->to[e];
+        F->skind[pos[e]] = F->kind[e];
+        F->twin[pos[e]] = pos[e ^ 1];
+    }
+    free(pos);
+    free(F->from); free(F->to); free(F->kind);
+    F->from = F->to = NULL;
+    F->kind = NULL;
+    return ORC_OK;
+}
+
+/* Capacities for alpha = p / q (all scaled by q); twins start empty. */
 static void fn_capacities(fnet* F, const uint64_t* deg, int h, u128 p, u128 q) {
     const u128 inf = (u128)1 << 120;
-    for (uint64_t e = 0; e < F->E; e += 2) {
-        uint32_t u = F->to[e + 1];
+    for (uint64_t a = 0; a < F->E; a++) {
         u128 c = 0;
-        switch (F->kind[e]) {
-            case ARC_S: c = q * deg[F->to[e] - 2]; break;
+        switch (F->skind[a]) {
+            case ARC_S: c = q * deg[F->head[a] - 2]; break;
             case ARC_T: c = p * (u128)h; break;
             case ARC_Q: c = q; break;
             case ARC_INF: c = inf; break;
         }
-        (void)u;
-        F->cap[e] = c;
-        F->cap[e + 1] = 0;
+        F->cap[a] = c;
     }
 }
 
@@ -854,9 +884,9 @@ static int fn_bfs(fnet* F) {
     F->queue[qt++] = 0;
     while (qh < qt) {
         uint32_t u = F->queue[qh++];
-        for (int64_t e = F->head[u]; e >= 0; e = F->next[e]) {
-            uint32_t v = F->to[e];
-            if (F->cap[e] > 0 && F->level[v] < 0) {
+        for (uint64_t a = F->first[u]; a < F->first[u + 1]; a++) {
+            uint32_t v = F->head[a];
+            if (F->cap[a] > 0 && F->level[v] < 0) {
                 F->level[v] = F->level[u] + 1;
                 F->queue[qt++] = v;
             }
@@ -869,32 +899,32 @@ static int fn_bfs(fnet* F) {
  * graph is found by an explicit-stack depth-first search. */
 static int fn_maxflow(fnet* F, u128* flow_out) {
     uint32_t* pnode = (uint32_t*)malloc((size_t)F->N * sizeof(uint32_t));
-    int64_t* parc = (int64_t*)malloc((size_t)F->N * sizeof(int64_t));
+    uint64_t* parc = (uint64_t*)malloc((size_t)F->N * sizeof(uint64_t));
     if (!pnode || !parc) { free(pnode); free(parc); return ORC_ENOMEM; }
     u128 flow = 0;
     while (fn_bfs(F)) {
-        for (uint32_t x = 0; x < F->N; x++) F->it[x] = F->head[x];
+        for (uint32_t x = 0; x < F->N; x++) F->it[x] = F->first[x];
         for (;;) {
             uint32_t depth = 0, u = 0;
             int found = 0;
             for (;;) {
                 if (u == 1) { found = 1; break; }
-                int64_t e = F->it[u];
-                while (e >= 0 && !(F->cap[e] > 0 && F->level[F->to[e]] == F->level[u] + 1))
-                    e = F->next[e];
-                F->it[u] = e;
-                if (e < 0) {                      /* dead end: retreat */
+                uint64_t a = F->it[u], end = F->first[u + 1];
+                while (a < end && !(F->cap[a] > 0 && F->level[F->head[a]] == F->level[u] + 1))
+                    a++;
+                F->it[u] = a;
+                if (a == end) {                   /* dead end: retreat */
                     F->level[u] = -1;
                     if (depth == 0) break;
                     depth--;
                     u = pnode[depth];
-                    F->it[u] = F->next[parc[depth]];
+                    F->it[u] = parc[depth] + 1;
                     continue;
                 }
                 pnode[depth] = u;
-                parc[depth] = e;
+                parc[depth] = a;
                 depth++;
-                u = F->to[e];
+                u = F->head[a];
             }
             if (!found) break;
             u128 b = F->cap[parc[0]];
@@ -902,7 +932,7 @@ static int fn_maxflow(fnet* F, u128* flow_out) {
                 if (F->cap[parc[i]] < b) b = F->cap[parc[i]];
             for (uint32_t i = 0; i < depth; i++) {
                 F->cap[parc[i]] -= b;
-                F->cap[parc[i] ^ 1] += b;
+                F->cap[F->twin[parc[i]]] += b;
             }
             flow += b;
         }
@@ -922,9 +952,9 @@ static void fn_reach_t(fnet* F, uint8_t* mark) {
     F->queue[qt++] = 1;
     while (qh < qt) {
         uint32_t y = F->queue[qh++];
-        for (int64_t e = F->head[y]; e >= 0; e = F->next[e]) {
-            uint32_t x = F->to[e];            /* arc e: y -> x; its twin x -> y */
-            if (!mark[x] && F->cap[e ^ 1] > 0) {
+        for (uint64_t a = F->first[y]; a < F->first[y + 1]; a++) {
+            uint32_t x = F->head[a];          /* arc a: y -> x; its twin x -> y */
+            if (!mark[x] && F->cap[F->twin[a]] > 0) {
                 mark[x] = 1;
                 F->queue[qt++] = x;
             }
@@ -1005,7 +1035,7 @@ static int alg1_network(const wgraph* g, int h, uint64_t mu, fnet* F) {
         }
         for (uint32_t j = 0; j < k; j++) fn_arc(F, 2 + cn[j], node, ARC_Q);
     }
-    rc = F->E == E ? ORC_OK : -3;
+    rc = F->E == E ? fn_finish(F) : -3;
 out:
     free(C.store);
     lister_free(&C);

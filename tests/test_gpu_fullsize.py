@@ -3,7 +3,9 @@ benchmark times (edge list resident on the device, dsd_graph_from_edges +
 dsd_core_app with device outputs).
 
 * Chung-Lu n = 1,000,000 (10M draws, exponent 2.1, planted G(200, 0.5)),
-  h = 3: every output against the oracle, element by element.
+  h = 3: every output against the oracle, element by element, and the
+  CoreExact answer certified by one oracle cut of Algorithm 1's network on
+  the oracle's own (ceil(rho'),Psi)-core (which holds every densest set).
 * R-MAT scale 22, h = 4: the oracle cannot list its 1.2e11 4-cliques in
   test time, so the checks are sampled or structural -- the clique-degrees
   of sampled vertices against the oracle's per-vertex count, sum(deg) =
@@ -50,6 +52,8 @@ def test_cl1m_h3_full_parity(L, orc):
         deg, mu = g.clique_degrees(3)
         core, kmax = g.core_decompose(3)
         lk, ls, lm = g.level_stats(3)
+        ex = g.core_exact(3, mem="device")
+        ex["cds"] = ex["cds"].cpu().numpy().astype(np.uint32)
     wdeg, wmu = orc.clique_degrees(og, 3)
     assert mu == wmu and np.array_equal(deg, wdeg)
     wcore, wk = orc.core_decompose(og, 3)
@@ -61,6 +65,23 @@ def test_cl1m_h3_full_parity(L, orc):
     assert r["kmax_core_mu"] == w["kmax_core_mu"]
     assert r["best_k"] == w["best_k"] and np.array_equal(de, w["densest"])
     assert (r["densest_mu"], r["densest_size"]) == (w["densest_mu"], w["densest_size"])
+    # CoreExact, certified by the oracle: the returned set holds mu cliques,
+    # and one cut of Algorithm 1's network at alpha = mu/size on the oracle's
+    # own (ceil(rho'),Psi)-core -- which holds every densest set -- finds no
+    # set above alpha and has exactly this set as its largest source side.
+    # (The oracle's full bisection on this 986-vertex, 21M-triangle core
+    # would take ~45 such cuts.)
+    inD = np.zeros(n, bool)
+    inD[ex["cds"]] = True
+    assert ex["size"] == ex["cds"].size and orc.induced_clique_count(og, 3, inD) == ex["mu"]
+    k1 = -(-w["densest_mu"] // w["densest_size"])
+    keep = np.flatnonzero(wcore >= k1).astype(np.uint32)
+    mask = np.zeros(n, bool)
+    mask[keep] = True
+    nk, ks, kd = _induced(s, d, mask)
+    beats, side = orc.densest_check(orc.csr(nk, ks, kd), 3, ex["mu"], ex["size"])
+    assert not beats
+    assert np.array_equal(ex["cds"], keep[side])
 
 
 def _induced(s, d, keep_mask):
