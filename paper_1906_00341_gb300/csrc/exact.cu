@@ -47,7 +47,7 @@ __host__ __device__ constexpr uint8_t arc_kind(uint8_t own, uint8_t pair) {
 }
 // Arcs per node above which a block, not a warp, works on the node.
 constexpr uint64_t kBigArcs = 2048;
-constexpr int kBigThreads = 256;
+constexpr int kBigThreads = 1024;
 
 unsigned grid_for_n(uint64_t n, unsigned per_block = 256) {
     uint64_t b = (n + per_block - 1) / per_block;
@@ -984,7 +984,7 @@ dsd_status min_cut(const Net& net, int h, uint64_t p, uint64_t q, cudaStream_t s
     PR P;
     const uint64_t t0 = now_ns();
     const uint64_t limit_rounds = 4 * N + 100000;
-    const int kRoundsPerRelabel = 8;
+    const int kRoundsPerRelabel = 32;
     XSTEP(cut_alloc(&w, N, s));
     P.head = net.head;
     P.to = net.to;
