@@ -317,6 +317,45 @@ typedef struct {
  * the network or of the cut failed); DSD_ERR_CUDA. */
 dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact_info* info);
 
+/* ---------------------------------------------------- pattern densities */
+
+/* Sec. 6 generalises the h-clique to a pattern Psi: an instance is a copy of
+ * the pattern in G (pattern edges on graph edges, not necessarily induced),
+ * deg(v, Psi) the instances holding v, mu(G, Psi) the number of instances,
+ * and the (k,Psi)-cores, core numbers and CoreApp outputs follow as for
+ * cliques.  Two patterns, with the closed forms of the appendix on special
+ * patterns:
+ *   DSD_PATTERN_STAR,  x = 2..8: the x-star (a centre and x leaves);
+ *     deg(v) = C(d(v), x) + sum over neighbours u of C(d(u) - 1, x - 1);
+ *   DSD_PATTERN_LOOP4 (x ignored): the 4-vertex loop (4-cycle);
+ *     deg(v) = sum over w != v of C(c(v, w), 2), c = common neighbours.
+ * Counts are 64-bit (binomials wrap beyond 2^64, as in any 64-bit count).
+ * Errors: DSD_ERR_INVALID (NULL handle, unknown pattern, x out of range,
+ * bad mem), DSD_ERR_NOMEM, DSD_ERR_CUDA. */
+#define DSD_PATTERN_STAR 1
+#define DSD_PATTERN_LOOP4 2
+
+/* deg (n entries, may be NULL) and *mu (may be NULL), host or device per mem. */
+dsd_status dsd_pattern_degrees(dsd_graph* g, int pattern, int x, uint64_t* deg, uint64_t* mu,
+                               int mem);
+
+/* (k,Psi)-core numbers (core, n entries, may be NULL), *kmax (may be NULL),
+ * and the level records: for each distinct core value k ascending, |R_k|
+ * and mu(R_k, Psi) (arrays of capacity cap, may be NULL; *nlevels = the
+ * count, DSD_ERR_OVERFLOW when it exceeds cap, the first cap still written).
+ * Level-synchronous peeling: every alive vertex of pattern-degree <= k
+ * leaves at level k, k = max(k, least alive pattern-degree). */
+dsd_status dsd_pattern_core_decompose(dsd_graph* g, int pattern, int x, uint64_t* core,
+                                      uint64_t* kmax, uint64_t* level_k, uint32_t* level_size,
+                                      uint64_t* level_mu, uint32_t cap, uint32_t* nlevels,
+                                      int mem);
+
+/* CoreApp's outputs for the pattern (the fields of dsd_core_app_result; mu
+ * counts pattern instances): the (k_max,Psi)-core and the densest level set
+ * (ties: the larger k), each ascending, capacity n, may be NULL. */
+dsd_status dsd_pattern_core_app(dsd_graph* g, int pattern, int x, uint32_t* kmax_core,
+                                uint32_t* densest, int mem, dsd_core_app_result* r);
+
 /* ------------------------------------------------------------- batches */
 
 /* Many small graphs in one launch.  The paper treats one graph at a time;

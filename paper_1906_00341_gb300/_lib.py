@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libdsd.so")
 
 DSD_MEM_HOST = 0
 DSD_MEM_DEVICE = 1
+DSD_PATTERN_STAR = 1
+DSD_PATTERN_LOOP4 = 2
 DSD_NPHASES = 6
 PHASES = ("csr", "order_peel", "orient", "count", "peel", "extract")
 
@@ -117,6 +119,10 @@ SIGNATURES = {
     "dsd_core_app_topdown": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult),
                                     ctypes.POINTER(TopdownInfo)]),
     "dsd_core_exact": (_int, [_P, _int, _P, _int, ctypes.POINTER(ExactInfo)]),
+    "dsd_pattern_degrees": (_int, [_P, _int, _int, _P, _P, _int]),
+    "dsd_pattern_core_decompose": (_int, [_P, _int, _int, _P, _P, _P, _P, _P, _u32, _P, _int]),
+    "dsd_pattern_core_app": (_int, [_P, _int, _int, _P, _P, _int,
+                                    ctypes.POINTER(CoreAppResult)]),
 }
 
 PEEL_STATS = ("rounds", "levels", "items", "bytes", "barrier_ns", "barriers", "compactions",
@@ -394,6 +400,23 @@ def dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem):
     return r, info
 
 
+def dsd_pattern_degrees(g, pattern, x, deg_ptr, mu_ptr, mem):
+    _check(load().dsd_pattern_degrees(g, pattern, x, deg_ptr, mu_ptr, mem))
+
+
+def dsd_pattern_core_decompose(g, pattern, x, core_ptr, kmax_ptr, lk_ptr, ls_ptr, lm_ptr, cap,
+                               nl_ptr, mem):
+    _check(load().dsd_pattern_core_decompose(g, pattern, x, core_ptr, kmax_ptr, lk_ptr, ls_ptr,
+                                             lm_ptr, cap, nl_ptr, mem))
+
+
+def dsd_pattern_core_app(g, pattern, x, kcore_ptr, densest_ptr, mem):
+    r = CoreAppResult()
+    _check(load().dsd_pattern_core_app(g, pattern, x, kcore_ptr, densest_ptr, mem,
+                                       ctypes.byref(r)))
+    return r
+
+
 def dsd_core_exact(g, h, cds_ptr, mem):
     info = ExactInfo()
     _check(load().dsd_core_exact(g, h, cds_ptr, mem, ctypes.byref(info)))
@@ -649,6 +672,39 @@ class Graph:
         out["schedule"] = dict(passes=int(info.passes), sub_n=int(info.sub_n), x=int(info.x),
                                gamma_out=int(info.gamma_out), sub_m=int(info.sub_m))
         return out
+
+    # patterns (Sec. 6) -----------------------------------------------------
+    def pattern_degrees(self, pattern, x=0, mem="host"):
+        deg = self._alloc(self.n, 8, mem)
+        mu = self._alloc(1, 8, mem)
+        dsd_pattern_degrees(self.handle, pattern, x, self._ptr(deg), self._ptr(mu),
+                            self._memc(mem))
+        return deg[: self.n], int(mu[0])
+
+    def pattern_core_decompose(self, pattern, x=0):
+        """(core numbers, k_max, level k, |R_k|, mu(R_k)) for a pattern."""
+        core = np.zeros(max(self.n, 1), np.uint64)
+        km = np.zeros(1, np.uint64)
+        nl = np.zeros(1, np.uint32)
+        cap = max(self.n, 1)
+        lk = np.zeros(cap, np.uint64)
+        ls = np.zeros(cap, np.uint32)
+        lm = np.zeros(cap, np.uint64)
+        dsd_pattern_core_decompose(self.handle, pattern, x, _np_ptr(core), _np_ptr(km),
+                                   _np_ptr(lk), _np_ptr(ls), _np_ptr(lm), cap, _np_ptr(nl),
+                                   DSD_MEM_HOST)
+        k = int(nl[0])
+        return core[: self.n], int(km[0]), lk[:k], ls[:k], lm[:k]
+
+    def pattern_core_app(self, pattern, x=0, mem="host"):
+        kc = self._alloc(self.n, 4, mem)
+        de = self._alloc(self.n, 4, mem)
+        r = dsd_pattern_core_app(self.handle, pattern, x, self._ptr(kc), self._ptr(de),
+                                 self._memc(mem))
+        return dict(kmax=int(r.kmax), kmax_core=kc[: r.kmax_core_size],
+                    kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                    densest=de[: r.densest_size], densest_mu=int(r.densest_mu),
+                    densest_size=int(r.densest_size), nlevels=int(r.nlevels))
 
     def core_exact(self, h, mem="host", sets=True):
         """CoreExact: rho_opt = mu / size and the largest densest set."""

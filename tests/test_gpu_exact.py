@@ -152,3 +152,57 @@ def test_exact_chung_lu_50k(L, orc, h):
     with L.Graph.from_edges(n, s, d) as g:
         r = g.core_exact(h)
     _check(r, _oracle_on_core(orc, og, h), h)
+
+
+def test_exact_many_components(L, orc):
+    # 40 disjoint planted blocks of 8..20 vertices in a sparse background; the
+    # densest blocks tie in pairs (equal sizes, both complete)
+    rng = np.random.default_rng(8600)
+    n, s, d = gg.er(6000, 0.0004, 8601)
+    verts = rng.permutation(n).astype(np.uint32)
+    at, src, dst = 0, [s], [d]
+    for b in range(40):
+        k = 8 + (b % 13)
+        blk = verts[at:at + k]
+        at += k
+        iu, ju = np.triu_indices(k, 1)
+        keep = (np.ones(iu.size, bool) if k >= 19 else rng.random(iu.size) < 0.8)
+        src.append(blk[iu[keep]])
+        dst.append(blk[ju[keep]])
+    s = np.concatenate(src).astype(np.uint32)
+    d = np.concatenate(dst).astype(np.uint32)
+    og = orc.csr(n, s, d)
+    for h in (2, 3, 4):
+        with L.Graph.from_edges(n, s, d) as g:
+            r = g.core_exact(h)
+        _check(r, orc.exact_cds(og, h), h)
+        assert r["components"] >= 1
+
+
+@pytest.mark.parametrize("h", [6, 7, 8])
+def test_exact_large_h(L, orc, h):
+    for seed in range(3):
+        n, s, d = gg.er(300, 0.03, 8700 + seed)
+        n, s, d, _ = gg.plant(n, s, d, 16 + seed, 0.85, 8800 + seed)
+        og = orc.csr(n, s, d)
+        with L.Graph.from_edges(n, s, d) as g:
+            r = g.core_exact(h)
+        _check(r, orc.exact_cds(og, h), (h, seed))
+
+
+def test_exact_wait_limit(L):
+    # the min cut checks the wait limit between its rounds: a 1 ms limit on a
+    # cut of ~50 ms ends it with DSD_ERR_TIMEOUT, and the handle and the
+    # context stay usable
+    n, s, d, _ = gg.workload("rmat14")
+    with L.Graph.from_edges(n, s, d) as g:
+        ref = g.core_exact(4)
+        L.dsd_set_wait_limit_ms(1)
+        try:
+            with pytest.raises(L.DSDError) as ei:
+                g.core_exact(4)
+            assert ei.value.name == "DSD_ERR_TIMEOUT"
+        finally:
+            L.dsd_set_wait_limit_ms(20000)
+        again = g.core_exact(4)
+    _check(again, ref)
