@@ -14,12 +14,13 @@
 //
 // (k,Psi)-cores by level-synchronous peeling: k <- max(k, least alive
 // degree); every alive vertex with degree <= k leaves at level k; the
-// degrees of the rest are recomputed; repeat.  Pattern-degrees only fall when
+// degrees of the alive vertices within two hops of them are recounted;
+// repeat.  Pattern-degrees only fall when
 // vertices leave, so the vertices leaving at level k are exactly
 // R_k \ R_{k+1} and the core numbers equal Algorithm 3's; the alive set at
 // the first round of a level k is R_k (level records for CoreApp's
-// outputs).  Each round recomputes every alive degree from scratch: simple
-// and exact; rounds are host-driven.
+// outputs).  Recounts use the same closed forms as the first count: exact;
+// rounds are host-driven.
 //
 // Every kernel reads and writes library-owned device buffers only; results
 // reach the caller through cudaMemcpyAsync.
@@ -146,17 +147,6 @@ __global__ void k_round_stats(uint32_t n, const uint8_t* alive, const unsigned l
     }
 }
 
-// Every alive vertex with degree <= k leaves with core number k.
-__global__ void k_retire(uint32_t n, uint8_t* alive, const unsigned long long* deg,
-                         unsigned long long k, unsigned long long* core) {
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x)
-        if (alive[v] && deg[v] <= k) {
-            core[v] = k;
-            alive[v] = 0;
-        }
-}
-
 __global__ void k_fill_u8(uint32_t n, uint8_t* a, uint8_t val) {
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x)
@@ -175,6 +165,141 @@ __global__ void k_compact_ids(uint32_t n, const uint32_t* flag, const uint64_t* 
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x)
         if (flag[v]) out[pos[v]] = (uint32_t)v;
+}
+
+__device__ __forceinline__ void warp_push(bool add, uint32_t x, uint32_t* out, uint32_t* n) {
+    unsigned b = __ballot_sync(0xffffffffu, add);
+    if (!b) return;
+    int leader = __ffs(b) - 1;
+    uint32_t base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(n, (uint32_t)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (add) out[base + __popc(b & ((1u << lane_id()) - 1u))] = x;
+}
+
+// Retire the level's frontier (core = k) and list it.
+__global__ void k_retire_list(uint32_t n, uint8_t* alive, const unsigned long long* deg,
+                              unsigned long long k, unsigned long long* core, uint32_t* lf,
+                              uint32_t* nf) {
+    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n;
+         x0 += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t v = x0 + threadIdx.x;
+        bool r = v < n && alive[v] && deg[v] <= k;
+        if (r) {
+            core[v] = k;
+            alive[v] = 0;
+        }
+        warp_push(r, (uint32_t)v, lf, nf);
+    }
+}
+
+// Alive neighbours of the listed vertices, each listed once per round
+// (stamp = round + 1).  Warp per listed vertex.
+__global__ void k_touch(const uint32_t* lin, const uint32_t* nin, const uint64_t* off,
+                        const uint32_t* adj, const uint8_t* alive, uint32_t* stamp,
+                        uint32_t mark, uint32_t* lout, uint32_t* nout) {
+    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t n = *nin;
+    for (uint64_t i = gw; i < n; i += nw) {
+        const uint32_t x = lin[i];
+        for (uint64_t p0 = off[x]; p0 < off[x + 1]; p0 += 32) {
+            uint64_t p = p0 + lane_id();
+            bool add = false;
+            uint32_t a = 0;
+            if (p < off[x + 1]) {
+                a = adj[p];
+                add = alive[a] && atomicMax(&stamp[a], mark) < mark;
+            }
+            warp_push(add, a, lout, nout);
+        }
+    }
+}
+
+// The listed vertices themselves, each once per round.
+__global__ void k_add(const uint32_t* lin, const uint32_t* nin, uint32_t* stamp, uint32_t mark,
+                      uint32_t* lout, uint32_t* nout) {
+    const uint32_t n = *nin;
+    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n;
+         x0 += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t i = x0 + threadIdx.x;
+        uint32_t a = i < n ? lin[i] : 0u;
+        bool add = i < n && atomicMax(&stamp[a], mark) < mark;
+        warp_push(add, a, lout, nout);
+    }
+}
+
+// Alive degree of the listed (alive) vertices.  Warp per entry.
+__global__ void k_alive_deg_list(const uint32_t* list, const uint32_t* nl, const uint64_t* off,
+                                 const uint32_t* adj, const uint8_t* alive, uint32_t* dal) {
+    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned lane = lane_id();
+    const uint32_t n = *nl;
+    for (uint64_t i = gw; i < n; i += nw) {
+        const uint32_t v = list[i];
+        unsigned c = 0;
+        for (uint64_t p = off[v] + lane; p < off[v + 1]; p += 32) c += alive[adj[p]];
+        c = warp_sum(c);
+        if (lane == 0) dal[v] = c;
+    }
+}
+
+// x-star degrees of the listed (alive) vertices.  Warp per entry.
+__global__ void k_star_deg_list(const uint32_t* list, const uint32_t* nl, const uint64_t* off,
+                                const uint32_t* adj, const uint8_t* alive, const uint32_t* dal,
+                                int x, unsigned long long* deg) {
+    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned lane = lane_id();
+    const uint32_t n = *nl;
+    for (uint64_t i = gw; i < n; i += nw) {
+        const uint32_t v = list[i];
+        unsigned long long sum = 0;
+        for (uint64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
+            uint32_t u = adj[p];
+            if (alive[u]) sum += binom((unsigned long long)dal[u] - 1, x - 1);
+        }
+        sum = warp_sum(sum);
+        if (lane == 0) deg[v] = sum + binom(dal[v], x);
+    }
+}
+
+// 4-loop degrees of the listed (alive) vertices (see k_loop_deg).  Block per
+// entry.
+__global__ void k_loop_deg_list(const uint32_t* list, const uint32_t* nl, uint32_t n,
+                                const uint64_t* off, const uint32_t* adj, const uint8_t* alive,
+                                uint32_t* cnt_all, unsigned long long* deg) {
+    __shared__ unsigned long long s_sum[32];
+    uint32_t* cnt = cnt_all + (uint64_t)blockIdx.x * n;
+    const unsigned nwarp = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
+    const uint32_t m = *nl;
+    for (uint64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        const uint32_t v = list[i];
+        unsigned long long sum = 0;
+        for (uint64_t p = off[v] + warp; p < off[v + 1]; p += nwarp) {
+            uint32_t a = adj[p];
+            if (!alive[a]) continue;
+            for (uint64_t q = off[a] + lane; q < off[a + 1]; q += 32) {
+                uint32_t w = adj[q];
+                if (w != v && alive[w]) sum += atomicAdd(&cnt[w], 1u);
+            }
+        }
+        sum = warp_sum(sum);
+        if (lane == 0) s_sum[warp] = sum;
+        __syncthreads();
+        for (uint64_t p = off[v] + warp; p < off[v + 1]; p += nwarp) {
+            uint32_t a = adj[p];
+            if (!alive[a]) continue;
+            for (uint64_t q = off[a] + lane; q < off[a + 1]; q += 32) cnt[adj[q]] = 0;
+        }
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (unsigned w = 0; w < nwarp; w++) t += s_sum[w];
+            deg[v] = t;
+        }
+        __syncthreads();
+    }
 }
 
 int pattern_size(int pattern, int x) { return pattern == kStar ? x + 1 : 4; }
@@ -205,10 +330,17 @@ struct PatWork {
     unsigned long long* stats = nullptr;
     uint32_t* cnt = nullptr;          // loop counters: blocks x n
     unsigned loop_blocks = 0;
+    uint32_t* stamp1 = nullptr;       // per-round marks (round + 1)
+    uint32_t* stamp2 = nullptr;
+    uint32_t* lf = nullptr;           // the round's frontier
+    uint32_t* l1 = nullptr;           // alive vertices next to it
+    uint32_t* lt = nullptr;           // alive vertices within two hops of it
+    uint32_t* ln = nullptr;           // lengths of lf, l1, lt
 };
 
 void pat_free(PatWork* w, cudaStream_t s) {
-    void* ptrs[] = {w->alive, w->dal, w->deg, w->core, w->stats, w->cnt};
+    void* ptrs[] = {w->alive, w->dal, w->deg, w->core, w->stats, w->cnt,
+                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln};
     for (void* p : ptrs) dev_free(p, s);
     *w = PatWork();
 }
@@ -219,6 +351,14 @@ dsd_status pat_alloc(PatWork* w, uint32_t n, int pattern, cudaStream_t s) {
     DSD_TRY(dalloc(&w->deg, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->core, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->stats, 4, s));
+    DSD_TRY(dalloc(&w->stamp1, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->stamp2, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->lf, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->l1, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->lt, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->ln, 4, s));
+    DSD_CU(cudaMemsetAsync(w->stamp1, 0, ((size_t)n + 1) * 4, s));
+    DSD_CU(cudaMemsetAsync(w->stamp2, 0, ((size_t)n + 1) * 4, s));
     if (pattern == kLoop && n) {
         // one counter row per block, at most ~1 GiB of rows
         uint64_t rows = (1ull << 28) / ((uint64_t)n + 1);
@@ -265,10 +405,11 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
     *kmax = 0;
     if (!n) return DSD_OK;
     k_fill_u8<<<pgrid(n), 256, 0, s>>>(n, w->alive, 1); note_launch();
+    DSD_TRY(degrees(g, pattern, x, w));
     uint64_t k = 0;
     bool first = true;
+    const unsigned gw = 152 * 8;
     for (uint32_t round = 0;; round++) {
-        DSD_TRY(degrees(g, pattern, x, w));
         unsigned long long init[3] = {~0ull, 0ull, 0ull}, st[3];
         DSD_CU(cudaMemcpyAsync(w->stats, init, sizeof(init), cudaMemcpyHostToDevice, s));
         k_round_stats<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats); note_launch();
@@ -282,12 +423,36 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
             L->mu.push_back(st[2] / (uint64_t)vs);
             first = false;
         }
-        k_retire<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, k, w->core); note_launch();
-        DSD_LAUNCHED();
-        if (round > n) {
+        if (round >= n) {
             set_error("pattern peel did not settle");
             return DSD_ERR_INTERNAL;
         }
+        // retire the frontier; only the alive vertices within two hops of it
+        // can lose instances (every instance through one of them and a
+        // frontier vertex spans at most two edges from it), so only they
+        // are recounted: l1 = alive neighbours of the frontier, lt = l1 plus
+        // their alive neighbours
+        const uint32_t mark = round + 1;
+        DSD_CU(cudaMemsetAsync(w->ln, 0, 16, s));
+        k_retire_list<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, k, w->core, w->lf, w->ln);
+        k_touch<<<gw, 256, 0, s>>>(w->lf, w->ln, g->off, g->adj, w->alive, w->stamp1, mark, w->l1,
+                                   w->ln + 1);
+        k_add<<<pgrid(n), 256, 0, s>>>(w->l1, w->ln + 1, w->stamp2, mark, w->lt, w->ln + 2);
+        k_touch<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->stamp2, mark,
+                                   w->lt, w->ln + 2);
+        for (int i = 0; i < 4; i++) note_launch();
+        if (pattern == kStar) {
+            k_alive_deg_list<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->dal);
+            k_star_deg_list<<<gw, 256, 0, s>>>(w->lt, w->ln + 2, g->off, g->adj, w->alive, w->dal,
+                                               x, w->deg);
+            note_launch();
+            note_launch();
+        } else {
+            k_loop_deg_list<<<w->loop_blocks, 256, 0, s>>>(w->lt, w->ln + 2, n, g->off, g->adj,
+                                                           w->alive, w->cnt, w->deg);
+            note_launch();
+        }
+        DSD_LAUNCHED();
     }
     *kmax = k;
     return DSD_OK;
