@@ -19,8 +19,9 @@
 // vertices leave, so the vertices leaving at level k are exactly
 // R_k \ R_{k+1} and the core numbers equal Algorithm 3's; the alive set at
 // the first round of a level k is R_k (level records for CoreApp's
-// outputs).  Recounts use the same closed forms as the first count: exact;
-// rounds are host-driven.
+// outputs).  Recounts use the same closed forms as the first count: exact.
+// The level k and the level records live on the device; the host launches
+// rounds in batches and reads back only to see whether anything is alive.
 //
 // Every kernel reads and writes library-owned device buffers only; results
 // reach the caller through cudaMemcpyAsync.
@@ -179,8 +180,9 @@ __device__ __forceinline__ void warp_push(bool add, uint32_t x, uint32_t* out, u
 
 // Retire the level's frontier (core = k) and list it.
 __global__ void k_retire_list(uint32_t n, uint8_t* alive, const unsigned long long* deg,
-                              unsigned long long k, unsigned long long* core, uint32_t* lf,
-                              uint32_t* nf) {
+                              const unsigned long long* st, unsigned long long* core,
+                              uint32_t* lf, uint32_t* nf) {
+    const unsigned long long k = st[3];
     for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n;
          x0 += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t v = x0 + threadIdx.x;
@@ -302,6 +304,39 @@ __global__ void k_loop_deg_list(const uint32_t* list, const uint32_t* nl, uint32
     }
 }
 
+// Device-side round state: st[0..2] the round's statistics (see
+// k_round_stats), st[3] the current level k, st[4] the number of level
+// records, st[5] 1 while no level has started, st[6] 1 once nothing is alive.
+__global__ void k_stats_reset(unsigned long long* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st[0] = ~0ull;
+        st[1] = 0;
+        st[2] = 0;
+    }
+}
+
+// After the statistics: stop when nothing is alive; else k = max(k, least
+// degree) and, when a level starts, its record (k, |R_k|, mu(R_k)).
+__global__ void k_level(unsigned long long* st, int vs, unsigned long long* lk,
+                        uint32_t* ls, unsigned long long* lm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (st[1] == 0) {
+        st[6] = 1;
+        return;
+    }
+    const unsigned long long mn = st[0];
+    if (st[5] || mn > st[3]) {
+        const unsigned long long k = st[5] ? mn : (mn > st[3] ? mn : st[3]);
+        const unsigned long long j = st[4];
+        lk[j] = k;
+        ls[j] = (uint32_t)st[1];
+        lm[j] = st[2] / (unsigned long long)vs;
+        st[4] = j + 1;
+        st[3] = k;
+        st[5] = 0;
+    }
+}
+
 int pattern_size(int pattern, int x) { return pattern == kStar ? x + 1 : 4; }
 
 dsd_status check_args(const dsd_graph* g, int pattern, int x, int mem) {
@@ -336,11 +371,15 @@ struct PatWork {
     uint32_t* l1 = nullptr;           // alive vertices next to it
     uint32_t* lt = nullptr;           // alive vertices within two hops of it
     uint32_t* ln = nullptr;           // lengths of lf, l1, lt
+    unsigned long long* lvk = nullptr;   // level records on the device
+    uint32_t* lvs = nullptr;
+    unsigned long long* lvm = nullptr;
 };
 
 void pat_free(PatWork* w, cudaStream_t s) {
     void* ptrs[] = {w->alive, w->dal, w->deg, w->core, w->stats, w->cnt,
-                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln};
+                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln,
+                    w->lvk, w->lvs, w->lvm};
     for (void* p : ptrs) dev_free(p, s);
     *w = PatWork();
 }
@@ -350,7 +389,10 @@ dsd_status pat_alloc(PatWork* w, uint32_t n, int pattern, cudaStream_t s) {
     DSD_TRY(dalloc(&w->dal, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->deg, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->core, (size_t)n + 1, s));
-    DSD_TRY(dalloc(&w->stats, 4, s));
+    DSD_TRY(dalloc(&w->stats, 8, s));
+    DSD_TRY(dalloc(&w->lvk, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->lvs, (size_t)n + 1, s));
+    DSD_TRY(dalloc(&w->lvm, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->stamp1, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->stamp2, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->lf, (size_t)n + 1, s));
@@ -406,27 +448,22 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
     if (!n) return DSD_OK;
     k_fill_u8<<<pgrid(n), 256, 0, s>>>(n, w->alive, 1); note_launch();
     DSD_TRY(degrees(g, pattern, x, w));
-    uint64_t k = 0;
-    bool first = true;
+    // st[3] = k = 0, st[4] = 0 records, st[5] = 1 (no level yet), st[6] = 0
+    const unsigned long long init[8] = {0, 0, 0, 0, 0, 1, 0, 0};
+    DSD_CU(cudaMemcpyAsync(w->stats, init, sizeof(init), cudaMemcpyHostToDevice, s));
     const unsigned gw = 152 * 8;
+    // rounds run on the device state without a readback; the host checks
+    // for the end every kBatch rounds (rounds after the end do nothing)
+    constexpr uint32_t kBatch = 32;
+    unsigned long long st[8];
     for (uint32_t round = 0;; round++) {
-        unsigned long long init[3] = {~0ull, 0ull, 0ull}, st[3];
-        DSD_CU(cudaMemcpyAsync(w->stats, init, sizeof(init), cudaMemcpyHostToDevice, s));
-        k_round_stats<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats); note_launch();
-        DSD_CU(cudaMemcpyAsync(st, w->stats, sizeof(st), cudaMemcpyDeviceToHost, s));
-        DSD_CU(cudaStreamSynchronize(s));
-        if (st[1] == 0) break;
-        if (first || st[0] > k) {
-            k = first ? st[0] : (st[0] > k ? st[0] : k);
-            L->k.push_back(k);
-            L->size.push_back((uint32_t)st[1]);
-            L->mu.push_back(st[2] / (uint64_t)vs);
-            first = false;
-        }
-        if (round >= n) {
+        if (round > n + kBatch) {
             set_error("pattern peel did not settle");
             return DSD_ERR_INTERNAL;
         }
+        k_stats_reset<<<1, 32, 0, s>>>(w->stats);
+        k_round_stats<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats);
+        k_level<<<1, 32, 0, s>>>(w->stats, vs, w->lvk, w->lvs, w->lvm);
         // retire the frontier; only the alive vertices within two hops of it
         // can lose instances (every instance through one of them and a
         // frontier vertex spans at most two edges from it), so only they
@@ -434,13 +471,14 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
         // their alive neighbours
         const uint32_t mark = round + 1;
         DSD_CU(cudaMemsetAsync(w->ln, 0, 16, s));
-        k_retire_list<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, k, w->core, w->lf, w->ln);
+        k_retire_list<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats, w->core, w->lf,
+                                               w->ln);
         k_touch<<<gw, 256, 0, s>>>(w->lf, w->ln, g->off, g->adj, w->alive, w->stamp1, mark, w->l1,
                                    w->ln + 1);
         k_add<<<pgrid(n), 256, 0, s>>>(w->l1, w->ln + 1, w->stamp2, mark, w->lt, w->ln + 2);
         k_touch<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->stamp2, mark,
                                    w->lt, w->ln + 2);
-        for (int i = 0; i < 4; i++) note_launch();
+        for (int i = 0; i < 7; i++) note_launch();
         if (pattern == kStar) {
             k_alive_deg_list<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->dal);
             k_star_deg_list<<<gw, 256, 0, s>>>(w->lt, w->ln + 2, g->off, g->adj, w->alive, w->dal,
@@ -453,8 +491,23 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
             note_launch();
         }
         DSD_LAUNCHED();
+        if ((round + 1) % kBatch == 0) {
+            DSD_CU(cudaMemcpyAsync(st, w->stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+            DSD_CU(cudaStreamSynchronize(s));
+            if (st[6]) break;
+        }
     }
-    *kmax = k;
+    const uint32_t nl = (uint32_t)st[4];
+    L->k.resize(nl);
+    L->size.resize(nl);
+    L->mu.resize(nl);
+    if (nl) {
+        DSD_CU(cudaMemcpyAsync(L->k.data(), w->lvk, (size_t)nl * 8, cudaMemcpyDeviceToHost, s));
+        DSD_CU(cudaMemcpyAsync(L->size.data(), w->lvs, (size_t)nl * 4, cudaMemcpyDeviceToHost, s));
+        DSD_CU(cudaMemcpyAsync(L->mu.data(), w->lvm, (size_t)nl * 8, cudaMemcpyDeviceToHost, s));
+        DSD_CU(cudaStreamSynchronize(s));
+    }
+    *kmax = st[3];
     return DSD_OK;
 }
 

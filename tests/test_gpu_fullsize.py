@@ -141,3 +141,45 @@ def og_src(og):
 
 def og_dst(og):
     return og.adj.astype(np.uint32)
+
+
+def test_cl4m_h3_learned_topdown_exact(L, orc):
+    """The learned leg's workload (Chung-Lu n = 4,000,000, 64M draws,
+    exponent 2.2, five planted G(300, 0.4)), h = 3: the plain, seeded
+    (trained proposal) and top-down CoreApp outputs against the oracle's
+    decomposition, and the CoreExact answer certified by one oracle cut on
+    the oracle's own (ceil(rho'),Psi)-core."""
+    from paper_1906_00341_gb300 import train
+    n, s, d, _ = gg.workload("cl4m")
+    og = orc.csr(n, s, d)
+    M = train.load_checkpoint(train.DEFAULT_CHECKPOINT)
+    g, keep = _device_graph(L, n, s, d)
+    outs = {}
+    with g:
+        assert g.m == og.m
+        outs["plain"] = g.core_app(3, mem="device")
+        outs["seeded"] = g.core_app_seeded(3, M, mem="device")
+        outs["topdown"] = g.core_app_topdown(3, mem="device")
+        ex = g.core_exact(3, mem="device")
+    assert outs["seeded"]["seed"]["accepted"] == 1
+    wcore, wk = orc.core_decompose(og, 3)
+    w = orc.core_app(og, 3, wcore, wk)
+    for name, r in outs.items():
+        assert r["kmax"] == w["kmax"], name
+        assert np.array_equal(r["kmax_core"].cpu().numpy().astype(np.uint32), w["kmax_core"]), name
+        assert r["kmax_core_mu"] == w["kmax_core_mu"], name
+        assert r["best_k"] == w["best_k"], name
+        assert np.array_equal(r["densest"].cpu().numpy().astype(np.uint32), w["densest"]), name
+        assert (r["densest_mu"], r["densest_size"]) == (w["densest_mu"], w["densest_size"]), name
+    cds = ex["cds"].cpu().numpy().astype(np.uint32)
+    inD = np.zeros(n, bool)
+    inD[cds] = True
+    assert ex["size"] == cds.size and orc.induced_clique_count(og, 3, inD) == ex["mu"]
+    k1 = -(-w["densest_mu"] // w["densest_size"])
+    keepv = np.flatnonzero(wcore >= k1).astype(np.uint32)
+    mask = np.zeros(n, bool)
+    mask[keepv] = True
+    nk, ks, kd = _induced(s, d, mask)
+    beats, side = orc.densest_check(orc.csr(nk, ks, kd), 3, ex["mu"], ex["size"])
+    assert not beats
+    assert np.array_equal(cds, keepv[side])
