@@ -514,7 +514,7 @@ def run_reference(args, rank, world):
             times.append(t)
     ms = 1e3 * float(np.mean(times))
     v = mu / (ms / 1e3)
-    sample = "induced subgraph on a seeded 50% vertex sample (n=%d, %d draws), h=%d" % (
+    sample = "induced subgraph on a seeded 50%% vertex sample (n=%d, %d draws), h=%d" % (
         ns, ss.size, args.h)
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "h-cliques/s",
