@@ -96,6 +96,24 @@ def test_closed_form_clique(L):
             assert kmax == math.comb(n - 1, h - 1) and set(core.tolist()) == {kmax}
 
 
+def test_large_clique_tiers(L):
+    # K_1500: every out-neighbourhood above the block bitmap size (1024) goes
+    # through the large h = 3 tier; one level holds every vertex
+    n = 1500
+    s, d = np.triu_indices(n, 1)
+    with L.Graph.from_edges(n, s.astype(np.uint32), d.astype(np.uint32)) as g:
+        for h in (2, 3):
+            deg, mu = g.clique_degrees(h)
+            assert mu == math.comb(n, h)
+            assert set(deg.tolist()) == {math.comb(n - 1, h - 1)}
+            core, kmax = g.core_decompose(h)
+            assert kmax == math.comb(n - 1, h - 1) and set(core.tolist()) == {kmax}
+            r = g.core_app(h)
+            assert r["densest_size"] == n and r["densest_mu"] == math.comb(n, h)
+        e = g.core_exact(2)   # (h = 3 would need a 3.4e9-arc network)
+        assert e["size"] == n and e["mu"] == math.comb(n, 2)
+
+
 def test_rejects_bad_input(L):
     with pytest.raises(L.DSDError) as ei:
         L.Graph.from_edges(5, np.array([0, 5], np.uint32), np.array([1, 1], np.uint32))
