@@ -47,6 +47,8 @@ METRIC = "(k,Ψ)-core decomposition ms & h-cliques/s; learned-seeded vs plain sp
 WORKLOAD = "cl1m"
 H = 3
 L2_BYTES = 129 * 1024 * 1024
+# side files of a run (clock samples, the batch launch-shape cache)
+OUT_DIR = os.environ.get("DSD_BENCH_DIR") or os.path.join(ROOT, "bench_out")
 
 
 def parse(argv=None):
@@ -112,7 +114,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.path.join(OUT_DIR, "clocks_bench.csv")
 
     def start(self):
         try:
@@ -416,7 +418,7 @@ def run_batched(args, local, graphs):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    cache = os.path.join(ROOT, "gpurun_out", "batch_autotune.txt")
+    cache = os.path.join(OUT_DIR, "batch_autotune.txt")
     B = L.Batch(graphs, want_cores=False, stream=stream, autotune_cache=cache)
     threads, cps, tuned = B.info()
     for _ in range(args.warmup):
