@@ -26,7 +26,7 @@ more objects on the same line (rank 0, skipped with --no-learned /
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the CPU oracle (tests' checker) on a bounded sample of
+--impl reference times the CPU oracle on a bounded sample of
 the same workload on the host cores.
 """
 from __future__ import annotations

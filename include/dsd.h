@@ -52,7 +52,7 @@ typedef enum {
     DSD_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
     DSD_ERR_TIMEOUT = 4,     /* a bounded inter-block wait ran out (see dsd_set_wait_limit_ms) */
     DSD_ERR_OVERFLOW = 5,    /* a result does not fit the caller's buffer or a counter overflowed */
-    DSD_ERR_UNSUPPORTED = 6, /* input outside what this build handles (message says why) */
+    DSD_ERR_UNSUPPORTED = 6, /* input outside what the library handles (message says why) */
     DSD_ERR_INTERNAL = 7
 } dsd_status;
 

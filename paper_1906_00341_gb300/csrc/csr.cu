@@ -52,7 +52,7 @@ dsd_status build_csr(dsd_graph* g, uint64_t m, const uint32_t* src, const uint32
     int sms = 152;
     DSD_TRY(num_sms(&sms));
     if ((m >> 31) != 0) {
-        set_error("edge lists of 2^31 or more entries are not supported by this build");
+        set_error("edge lists of 2^31 or more entries are not supported by this library");
         return DSD_ERR_UNSUPPORTED;
     }
     uint32_t* cnt = nullptr;      // [n] endpoint counts, then cursors
