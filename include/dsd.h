@@ -331,7 +331,8 @@ dsd_status dsd_core_exact(dsd_graph* g, int h, uint32_t* cds, int mem, dsd_exact
  *     deg(v) = sum over w != v of C(c(v, w), 2), c = common neighbours.
  * Counts are 64-bit (binomials wrap beyond 2^64, as in any 64-bit count).
  * Errors: DSD_ERR_INVALID (NULL handle, unknown pattern, x out of range,
- * bad mem), DSD_ERR_NOMEM, DSD_ERR_CUDA. */
+ * bad mem), DSD_ERR_NOMEM, DSD_ERR_TIMEOUT (a grid-barrier wait of the
+ * peel ran past the limit of dsd_set_wait_limit_ms), DSD_ERR_CUDA. */
 #define DSD_PATTERN_STAR 1
 #define DSD_PATTERN_LOOP4 2
 

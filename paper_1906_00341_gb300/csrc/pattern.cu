@@ -14,14 +14,17 @@
 //
 // (k,Psi)-cores by level-synchronous peeling: k <- max(k, least alive
 // degree); every alive vertex with degree <= k leaves at level k; the
-// degrees of the alive vertices within two hops of them are recounted;
+// degrees of the alive vertices within two hops of them are updated;
 // repeat.  Pattern-degrees only fall when
 // vertices leave, so the vertices leaving at level k are exactly
 // R_k \ R_{k+1} and the core numbers equal Algorithm 3's; the alive set at
 // the first round of a level k is R_k (level records for CoreApp's
 // outputs).  Recounts use the same closed forms as the first count: exact.
-// The level k and the level records live on the device; the host launches
-// rounds in batches and reads back only to see whether anything is alive.
+// All rounds run in one cooperative launch whose phases -- statistics,
+// level and retirement, the degree changes -- are separated by grid barriers
+// with bounded waits.  The degree changes are exact differences, not
+// recounts: for the x-star from the changed alive degrees, for the loop from
+// the destroyed loops, each charged to its smallest-id frontier member.
 //
 // Every kernel reads and writes library-owned device buffers only; results
 // reach the caller through cudaMemcpyAsync.
@@ -178,163 +181,256 @@ __device__ __forceinline__ void warp_push(bool add, uint32_t x, uint32_t* out, u
     if (add) out[base + __popc(b & ((1u << lane_id()) - 1u))] = x;
 }
 
-// Retire the level's frontier (core = k) and list it.
-__global__ void k_retire_list(uint32_t n, uint8_t* alive, const unsigned long long* deg,
-                              const unsigned long long* st, unsigned long long* core,
-                              uint32_t* lf, uint32_t* nf) {
-    const unsigned long long k = st[3];
-    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n;
-         x0 += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t v = x0 + threadIdx.x;
-        bool r = v < n && alive[v] && deg[v] <= k;
-        if (r) {
-            core[v] = k;
-            alive[v] = 0;
-        }
-        warp_push(r, (uint32_t)v, lf, nf);
-    }
-}
+// ------------------------------------------------------- persistent rounds
+// All rounds in one cooperative launch (one block per SM): the phases of a
+// round are separated by a grid barrier whose waits are bounded in time (a
+// wait past the limit sets the error flag; every block then leaves at its
+// next barrier).  The device-side round state (st, see k_level) is the same
+// as the launch-per-phase path's.
 
-// Alive neighbours of the listed vertices, each listed once per round
-// (stamp = round + 1).  Warp per listed vertex.
-__global__ void k_touch(const uint32_t* lin, const uint32_t* nin, const uint64_t* off,
-                        const uint32_t* adj, const uint8_t* alive, uint32_t* stamp,
-                        uint32_t mark, uint32_t* lout, uint32_t* nout) {
-    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t n = *nin;
-    for (uint64_t i = gw; i < n; i += nw) {
-        const uint32_t x = lin[i];
-        for (uint64_t p0 = off[x]; p0 < off[x + 1]; p0 += 32) {
-            uint64_t p = p0 + lane_id();
-            bool add = false;
-            uint32_t a = 0;
-            if (p < off[x + 1]) {
-                a = adj[p];
-                add = alive[a] && atomicMax(&stamp[a], mark) < mark;
-            }
-            warp_push(add, a, lout, nout);
-        }
-    }
-}
+struct PatCtrl {
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    uint32_t error;
+    uint32_t rounds;
+};
 
-// The listed vertices themselves, each once per round.
-__global__ void k_add(const uint32_t* lin, const uint32_t* nin, uint32_t* stamp, uint32_t mark,
-                      uint32_t* lout, uint32_t* nout) {
-    const uint32_t n = *nin;
-    for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n;
-         x0 += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t i = x0 + threadIdx.x;
-        uint32_t a = i < n ? lin[i] : 0u;
-        bool add = i < n && atomicMax(&stamp[a], mark) < mark;
-        warp_push(add, a, lout, nout);
-    }
-}
+struct PatRun {
+    uint32_t n;
+    int pattern, x, vs;
+    const uint64_t* off;
+    const uint32_t* adj;
+    uint8_t* alive;
+    uint32_t* dal;
+    unsigned long long* deg;
+    unsigned long long* core;
+    unsigned long long* st;
+    unsigned long long* lvk;
+    uint32_t* lvs;
+    unsigned long long* lvm;
+    uint32_t* stamp1;
+    uint32_t* stamp2;
+    uint32_t* lf;
+    uint32_t* l1;
+    uint32_t* lt;
+    uint32_t* ln;
+    uint32_t* gone;           // star: frontier neighbours lost this round
+    uint32_t* cnt;
+    uint32_t cnt_rows;        // blocks with a loop counter row
+    PatCtrl* ctrl;
+    uint64_t wait_ns;
+};
 
-// Alive degree of the listed (alive) vertices.  Warp per entry.
-__global__ void k_alive_deg_list(const uint32_t* list, const uint32_t* nl, const uint64_t* off,
-                                 const uint32_t* adj, const uint8_t* alive, uint32_t* dal) {
-    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned lane = lane_id();
-    const uint32_t n = *nl;
-    for (uint64_t i = gw; i < n; i += nw) {
-        const uint32_t v = list[i];
-        unsigned c = 0;
-        for (uint64_t p = off[v] + lane; p < off[v + 1]; p += 32) c += alive[adj[p]];
-        c = warp_sum(c);
-        if (lane == 0) dal[v] = c;
-    }
-}
-
-// x-star degrees of the listed (alive) vertices.  Warp per entry.
-__global__ void k_star_deg_list(const uint32_t* list, const uint32_t* nl, const uint64_t* off,
-                                const uint32_t* adj, const uint8_t* alive, const uint32_t* dal,
-                                int x, unsigned long long* deg) {
-    uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned lane = lane_id();
-    const uint32_t n = *nl;
-    for (uint64_t i = gw; i < n; i += nw) {
-        const uint32_t v = list[i];
-        unsigned long long sum = 0;
-        for (uint64_t p = off[v] + lane; p < off[v + 1]; p += 32) {
-            uint32_t u = adj[p];
-            if (alive[u]) sum += binom((unsigned long long)dal[u] - 1, x - 1);
-        }
-        sum = warp_sum(sum);
-        if (lane == 0) deg[v] = sum + binom(dal[v], x);
-    }
-}
-
-// 4-loop degrees of the listed (alive) vertices (see k_loop_deg).  Block per
-// entry.
-__global__ void k_loop_deg_list(const uint32_t* list, const uint32_t* nl, uint32_t n,
-                                const uint64_t* off, const uint32_t* adj, const uint8_t* alive,
-                                uint32_t* cnt_all, unsigned long long* deg) {
-    __shared__ unsigned long long s_sum[32];
-    uint32_t* cnt = cnt_all + (uint64_t)blockIdx.x * n;
-    const unsigned nwarp = blockDim.x >> 5, warp = warp_id(), lane = lane_id();
-    const uint32_t m = *nl;
-    for (uint64_t i = blockIdx.x; i < m; i += gridDim.x) {
-        const uint32_t v = list[i];
-        unsigned long long sum = 0;
-        for (uint64_t p = off[v] + warp; p < off[v + 1]; p += nwarp) {
-            uint32_t a = adj[p];
-            if (!alive[a]) continue;
-            for (uint64_t q = off[a] + lane; q < off[a + 1]; q += 32) {
-                uint32_t w = adj[q];
-                if (w != v && alive[w]) sum += atomicAdd(&cnt[w], 1u);
+__device__ bool pat_barrier(PatCtrl* c, uint64_t wait_ns) {
+    __shared__ uint32_t s_err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t_in = globaltimer_ns();
+        volatile uint32_t* genp = &c->bar_gen;
+        const uint32_t gen = *genp;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            c->bar_count = 0;
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (*genp == gen) {
+                if (((++spins) & 255u) == 0 && globaltimer_ns() - t_in > wait_ns) {
+                    atomicOr(&c->error, 1u);
+                    break;
+                }
+                if (*(volatile uint32_t*)&c->error) break;
             }
         }
-        sum = warp_sum(sum);
-        if (lane == 0) s_sum[warp] = sum;
-        __syncthreads();
-        for (uint64_t p = off[v] + warp; p < off[v + 1]; p += nwarp) {
-            uint32_t a = adj[p];
-            if (!alive[a]) continue;
-            for (uint64_t q = off[a] + lane; q < off[a + 1]; q += 32) cnt[adj[q]] = 0;
-        }
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0;
-            for (unsigned w = 0; w < nwarp; w++) t += s_sum[w];
-            deg[v] = t;
-        }
-        __syncthreads();
+        __threadfence();
+        s_err = *(volatile uint32_t*)&c->error;
     }
+    __syncthreads();
+    return s_err == 0;
 }
 
-// Device-side round state: st[0..2] the round's statistics (see
-// k_round_stats), st[3] the current level k, st[4] the number of level
-// records, st[5] 1 while no level has started, st[6] 1 once nothing is alive.
-__global__ void k_stats_reset(unsigned long long* st) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st[0] = ~0ull;
-        st[1] = 0;
-        st[2] = 0;
+__global__ void __launch_bounds__(256) k_pattern_rounds(PatRun R) {
+    __shared__ unsigned long long s_red[3][8];
+    const unsigned lane = lane_id(), warp = warp_id();
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gwarp = tid >> 5, nwarps = nthreads >> 5;
+    const uint32_t n = R.n;
+    unsigned long long* st = R.st;
+    for (uint32_t round = 0; round <= n; round++) {
+        // ---- statistics of the alive vertices (st[0..2] are zero / ~0 here)
+        {
+            unsigned long long mn = ~0ull, cnt = 0, sum = 0;
+            for (uint64_t v = tid; v < n; v += nthreads)
+                if (R.alive[v]) {
+                    mn = R.deg[v] < mn ? R.deg[v] : mn;
+                    cnt++;
+                    sum += R.deg[v];
+                }
+            mn = warp_min_u64(mn);
+            cnt = warp_sum(cnt);
+            sum = warp_sum(sum);
+            if (lane == 0) {
+                s_red[0][warp] = mn;
+                s_red[1][warp] = cnt;
+                s_red[2][warp] = sum;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (unsigned w = 1; w < (blockDim.x >> 5); w++) {
+                    mn = s_red[0][w] < s_red[0][0] ? s_red[0][w] : s_red[0][0];
+                    s_red[0][0] = mn;
+                    s_red[1][0] += s_red[1][w];
+                    s_red[2][0] += s_red[2][w];
+                }
+                if (s_red[0][0] != ~0ull) atomicMin(&st[0], s_red[0][0]);
+                if (s_red[1][0]) atomicAdd(&st[1], s_red[1][0]);
+                if (s_red[2][0]) atomicAdd(&st[2], s_red[2][0]);
+            }
+            if (blockIdx.x == 0 && threadIdx.x < 3) R.ln[threadIdx.x] = 0;
+        }
+        if (!pat_barrier(R.ctrl, R.wait_ns)) return;
+        // ---- level (every block decides alike from st); retire the frontier
+        const unsigned long long amin = *(volatile unsigned long long*)&st[0];
+        const unsigned long long acnt = *(volatile unsigned long long*)&st[1];
+        const unsigned long long asum = *(volatile unsigned long long*)&st[2];
+        if (acnt == 0) {
+            if (tid == 0) {
+                st[6] = 1;
+                R.ctrl->rounds = round;
+            }
+            return;
+        }
+        const unsigned long long k0 = *(volatile unsigned long long*)&st[3];
+        const bool fresh = *(volatile unsigned long long*)&st[5] != 0;
+        unsigned long long k = k0;
+        if (fresh || amin > k0) {
+            k = fresh ? amin : (amin > k0 ? amin : k0);
+            if (tid == 0) {
+                const unsigned long long j = st[4];
+                R.lvk[j] = k;
+                R.lvs[j] = (uint32_t)acnt;
+                R.lvm[j] = asum / (unsigned long long)R.vs;
+            }
+        }
+        const uint32_t mark = round + 1;
+        for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x; x0 < n; x0 += nthreads) {
+            const uint64_t v = x0 + threadIdx.x;
+            bool r = v < n && R.alive[v] && R.deg[v] <= k;
+            if (r) {
+                R.core[v] = k;
+                R.alive[v] = 0;
+                R.stamp1[v] = mark;   // a frontier member of this round
+            }
+            warp_push(r, (uint32_t)v, R.lf, R.ln);
+        }
+        if (!pat_barrier(R.ctrl, R.wait_ns)) return;
+        // ---- level state for the next round
+        if (tid == 0) {
+            if (fresh || amin > k0) {
+                st[4] += 1;
+                st[3] = k;
+                st[5] = 0;
+            }
+            st[0] = ~0ull;
+            st[1] = 0;
+            st[2] = 0;
+        }
+        const uint32_t nf = *(volatile uint32_t*)&R.ln[0];
+        if (R.pattern == kStar) {
+            // x-star: deg(v) = C(d(v), x) + sum over alive neighbours u of
+            // C(d(u) - 1, x - 1) depends only on alive degrees, so the
+            // round's change is applied as exact differences:
+            //   (a) every alive v next to a frontier vertex f loses f's term
+            //       C(d(f) - 1, x - 1), and u = v counts its lost neighbours;
+            //   (b) every such u (its degree d -> d') changes its own term
+            //       by C(d', x) - C(d, x) and each alive neighbour's term by
+            //       C(d' - 1, x - 1) - C(d - 1, x - 1).
+            // Sums wrap modulo 2^64 like the counts themselves.
+            for (uint64_t i = gwarp; i < nf; i += nwarps) {
+                const uint32_t f = R.lf[i];
+                const unsigned long long lost = binom((unsigned long long)R.dal[f] - 1, R.x - 1);
+                for (uint64_t p0 = R.off[f]; p0 < R.off[f + 1]; p0 += 32) {
+                    const uint64_t p = p0 + lane;
+                    bool add = false;
+                    uint32_t a = 0;
+                    if (p < R.off[f + 1]) {
+                        a = R.adj[p];
+                        if (R.alive[a]) {
+                            atomicAdd(&R.deg[a], 0ull - lost);
+                            atomicAdd(&R.gone[a], 1u);
+                            add = atomicMax(&R.stamp1[a], mark) < mark;
+                        }
+                    }
+                    warp_push(add, a, R.l1, R.ln + 1);
+                }
+            }
+            if (!pat_barrier(R.ctrl, R.wait_ns)) return;
+            const uint32_t n1 = *(volatile uint32_t*)&R.ln[1];
+            for (uint64_t i = gwarp; i < n1; i += nwarps) {
+                const uint32_t u = R.l1[i];
+                const unsigned long long d0 = R.dal[u], d1 = d0 - R.gone[u];
+                const unsigned long long dn = binom(d1 - 1, R.x - 1) - binom(d0 - 1, R.x - 1);
+                for (uint64_t p = R.off[u] + lane; p < R.off[u + 1]; p += 32) {
+                    const uint32_t v = R.adj[p];
+                    if (R.alive[v] && dn) atomicAdd(&R.deg[v], dn);
+                }
+                if (lane == 0) {
+                    atomicAdd(&R.deg[u], binom(d1, R.x) - binom(d0, R.x));
+                    R.dal[u] = (uint32_t)d1;
+                    R.gone[u] = 0;
+                }
+            }
+            if (!pat_barrier(R.ctrl, R.wait_ns)) return;
+            continue;
+        }
+        // ---- 4-loop: every destroyed loop is charged once, to its
+        // smallest-id frontier member f: from f, the loops f - a - w - b
+        // whose other members are alive or larger frontier members.
+        // Grouping the 2-paths f - a - w by w (c(w) of them), each alive a
+        // loses c(w) - 1 loops and each alive w loses C(c(w), 2) -- the
+        // appendix's decrements, made exact under simultaneous removal by
+        // the single charge.  A block per frontier vertex, with its private
+        // counter row (zero between uses).
+        if (blockIdx.x < R.cnt_rows) {
+            uint32_t* cnt = R.cnt + (uint64_t)blockIdx.x * n;
+            const unsigned nwarp = blockDim.x >> 5;
+            auto valid = [&](uint32_t y, uint32_t f) -> bool {
+                return R.alive[y] || (R.stamp1[y] == mark && y > f);
+            };
+            for (uint64_t i = blockIdx.x; i < nf; i += R.cnt_rows) {
+                const uint32_t f = R.lf[i];
+                for (int pass = 0; pass < 3; pass++) {
+                    for (uint64_t p = R.off[f] + warp; p < R.off[f + 1]; p += nwarp) {
+                        const uint32_t a = R.adj[p];
+                        if (!valid(a, f)) continue;
+                        const bool a_alive = R.alive[a];
+                        for (uint64_t q = R.off[a] + lane; q < R.off[a + 1]; q += 32) {
+                            const uint32_t w = R.adj[q];
+                            if (w == f || !valid(w, f)) continue;
+                            if (pass == 0) {
+                                atomicAdd(&cnt[w], 1u);
+                            } else if (pass == 1) {
+                                const uint32_t c = cnt[w];
+                                if (a_alive && c > 1)
+                                    atomicAdd(&R.deg[a], 0ull - (unsigned long long)(c - 1));
+                            } else {
+                                const uint32_t c = atomicExch(&cnt[w], 0u);
+                                if (c > 1 && R.alive[w])
+                                    atomicAdd(&R.deg[w],
+                                              0ull - (unsigned long long)c * (c - 1) / 2);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        if (!pat_barrier(R.ctrl, R.wait_ns)) return;
     }
-}
-
-// After the statistics: stop when nothing is alive; else k = max(k, least
-// degree) and, when a level starts, its record (k, |R_k|, mu(R_k)).
-__global__ void k_level(unsigned long long* st, int vs, unsigned long long* lk,
-                        uint32_t* ls, unsigned long long* lm) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (st[1] == 0) {
-        st[6] = 1;
-        return;
-    }
-    const unsigned long long mn = st[0];
-    if (st[5] || mn > st[3]) {
-        const unsigned long long k = st[5] ? mn : (mn > st[3] ? mn : st[3]);
-        const unsigned long long j = st[4];
-        lk[j] = k;
-        ls[j] = (uint32_t)st[1];
-        lm[j] = st[2] / (unsigned long long)vs;
-        st[4] = j + 1;
-        st[3] = k;
-        st[5] = 0;
-    }
+    if (tid == 0) atomicOr(&R.ctrl->error, 2u);   // more rounds than vertices
 }
 
 int pattern_size(int pattern, int x) { return pattern == kStar ? x + 1 : 4; }
@@ -371,6 +467,7 @@ struct PatWork {
     uint32_t* l1 = nullptr;           // alive vertices next to it
     uint32_t* lt = nullptr;           // alive vertices within two hops of it
     uint32_t* ln = nullptr;           // lengths of lf, l1, lt
+    uint32_t* gone = nullptr;         // per vertex, zero between rounds
     unsigned long long* lvk = nullptr;   // level records on the device
     uint32_t* lvs = nullptr;
     unsigned long long* lvm = nullptr;
@@ -378,7 +475,7 @@ struct PatWork {
 
 void pat_free(PatWork* w, cudaStream_t s) {
     void* ptrs[] = {w->alive, w->dal, w->deg, w->core, w->stats, w->cnt,
-                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln,
+                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln, w->gone,
                     w->lvk, w->lvs, w->lvm};
     for (void* p : ptrs) dev_free(p, s);
     *w = PatWork();
@@ -399,6 +496,8 @@ dsd_status pat_alloc(PatWork* w, uint32_t n, int pattern, cudaStream_t s) {
     DSD_TRY(dalloc(&w->l1, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->lt, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->ln, 4, s));
+    DSD_TRY(dalloc(&w->gone, (size_t)n + 1, s));
+    DSD_CU(cudaMemsetAsync(w->gone, 0, ((size_t)n + 1) * 4, s));
     DSD_CU(cudaMemsetAsync(w->stamp1, 0, ((size_t)n + 1) * 4, s));
     DSD_CU(cudaMemsetAsync(w->stamp2, 0, ((size_t)n + 1) * 4, s));
     if (pattern == kLoop && n) {
@@ -448,54 +547,73 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
     if (!n) return DSD_OK;
     k_fill_u8<<<pgrid(n), 256, 0, s>>>(n, w->alive, 1); note_launch();
     DSD_TRY(degrees(g, pattern, x, w));
-    // st[3] = k = 0, st[4] = 0 records, st[5] = 1 (no level yet), st[6] = 0
-    const unsigned long long init[8] = {0, 0, 0, 0, 0, 1, 0, 0};
-    DSD_CU(cudaMemcpyAsync(w->stats, init, sizeof(init), cudaMemcpyHostToDevice, s));
-    const unsigned gw = 152 * 8;
-    // rounds run on the device state without a readback; the host checks
-    // for the end every kBatch rounds (rounds after the end do nothing)
-    constexpr uint32_t kBatch = 32;
-    unsigned long long st[8];
-    for (uint32_t round = 0;; round++) {
-        if (round > n + kBatch) {
-            set_error("pattern peel did not settle");
-            return DSD_ERR_INTERNAL;
-        }
-        k_stats_reset<<<1, 32, 0, s>>>(w->stats);
-        k_round_stats<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats);
-        k_level<<<1, 32, 0, s>>>(w->stats, vs, w->lvk, w->lvs, w->lvm);
-        // retire the frontier; only the alive vertices within two hops of it
-        // can lose instances (every instance through one of them and a
-        // frontier vertex spans at most two edges from it), so only they
-        // are recounted: l1 = alive neighbours of the frontier, lt = l1 plus
-        // their alive neighbours
-        const uint32_t mark = round + 1;
-        DSD_CU(cudaMemsetAsync(w->ln, 0, 16, s));
-        k_retire_list<<<pgrid(n), 256, 0, s>>>(n, w->alive, w->deg, w->stats, w->core, w->lf,
-                                               w->ln);
-        k_touch<<<gw, 256, 0, s>>>(w->lf, w->ln, g->off, g->adj, w->alive, w->stamp1, mark, w->l1,
-                                   w->ln + 1);
-        k_add<<<pgrid(n), 256, 0, s>>>(w->l1, w->ln + 1, w->stamp2, mark, w->lt, w->ln + 2);
-        k_touch<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->stamp2, mark,
-                                   w->lt, w->ln + 2);
-        for (int i = 0; i < 7; i++) note_launch();
-        if (pattern == kStar) {
-            k_alive_deg_list<<<gw, 256, 0, s>>>(w->l1, w->ln + 1, g->off, g->adj, w->alive, w->dal);
-            k_star_deg_list<<<gw, 256, 0, s>>>(w->lt, w->ln + 2, g->off, g->adj, w->alive, w->dal,
-                                               x, w->deg);
-            note_launch();
-            note_launch();
-        } else {
-            k_loop_deg_list<<<w->loop_blocks, 256, 0, s>>>(w->lt, w->ln + 2, n, g->off, g->adj,
-                                                           w->alive, w->cnt, w->deg);
-            note_launch();
-        }
-        DSD_LAUNCHED();
-        if ((round + 1) % kBatch == 0) {
-            DSD_CU(cudaMemcpyAsync(st, w->stats, sizeof(st), cudaMemcpyDeviceToHost, s));
-            DSD_CU(cudaStreamSynchronize(s));
-            if (st[6]) break;
-        }
+    // st[0..2] the statistics (min ~0), st[3] = k = 0, st[4] = 0 records,
+    // st[5] = 1 (no level yet), st[6] = 0
+    const unsigned long long init[8] = {~0ull, 0, 0, 0, 0, 1, 0, 0};
+    unsigned long long st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    PatCtrl* ctrl = nullptr;
+    DSD_TRY(dalloc(&ctrl, 1, s));
+    int sms = 152;
+    dsd_status rs = num_sms(&sms);
+    int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    if (rs == DSD_OK) {
+        e = cudaMemcpyAsync(w->stats, init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, sizeof(PatCtrl), s);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pattern_rounds, 256, 0);
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    }
+    PatCtrl hc;
+    memset(&hc, 0, sizeof(hc));
+    if (rs == DSD_OK && e == cudaSuccess) {
+        PatRun R;
+        R.n = n;
+        R.pattern = pattern;
+        R.x = x;
+        R.vs = vs;
+        R.off = g->off;
+        R.adj = g->adj;
+        R.alive = w->alive;
+        R.dal = w->dal;
+        R.deg = w->deg;
+        R.core = w->core;
+        R.st = w->stats;
+        R.lvk = w->lvk;
+        R.lvs = w->lvs;
+        R.lvm = w->lvm;
+        R.stamp1 = w->stamp1;
+        R.stamp2 = w->stamp2;
+        R.lf = w->lf;
+        R.l1 = w->l1;
+        R.lt = w->lt;
+        R.ln = w->ln;
+        R.gone = w->gone;
+        R.cnt = w->cnt;
+        R.ctrl = ctrl;
+        R.wait_ns = wait_limit_ns();
+        // x-star: one block per SM (the fewest barrier arrivals); 4-loop: up
+        // to 4 (its decrements run a block per frontier vertex)
+        const unsigned per = pattern == kLoop ? (unsigned)(per_sm < 4 ? per_sm : 4) : 1u;
+        const unsigned grid = (unsigned)sms * per;
+        R.cnt_rows = pattern == kLoop ? (w->loop_blocks < grid ? w->loop_blocks : grid) : 0;
+        void* args[] = {&R};
+        e = cudaLaunchCooperativeKernel((void*)k_pattern_rounds, dim3(grid), dim3(256), args, 0, s);
+        note_launch();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(st, w->stats, sizeof(st), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    dev_free(ctrl, s);
+    DSD_TRY(rs);
+    if (e != cudaSuccess) return cuda_fail(e, "pattern rounds", __FILE__, __LINE__);
+    if (hc.error & 1u) {
+        set_error("pattern peel: a grid barrier wait ran past the limit");
+        return DSD_ERR_TIMEOUT;
+    }
+    if (hc.error || !st[6]) {
+        set_error("pattern peel did not settle");
+        return DSD_ERR_INTERNAL;
     }
     const uint32_t nl = (uint32_t)st[4];
     L->k.resize(nl);

@@ -87,3 +87,12 @@ def test_pattern_degenerate_and_device(L, orc):
             g.pattern_degrees(L.DSD_PATTERN_STAR, 1)
         with pytest.raises(L.DSDError):
             g.pattern_degrees(7, 2)
+
+
+@pytest.mark.parametrize("name,x", [("star", 2), ("star", 3), ("loop", 0)])
+def test_pattern_power_law(L, orc, name, x):
+    # hubs: a frontier vertex next to a hub changes the counts of the hub's
+    # whole neighbourhood; many levels with several vertices leaving at once
+    n, s, d = gg.chung_lu(2000, 16000, 2.1, 200.0, 9501)
+    n, s, d, _ = gg.plant(n, s, d, 30, 0.5, 9502)
+    _compare(L, orc, n, s, d, name, x, (name, x, "power law"))
