@@ -209,10 +209,8 @@ struct PatRun {
     uint32_t* lvs;
     unsigned long long* lvm;
     uint32_t* stamp1;
-    uint32_t* stamp2;
     uint32_t* lf;
     uint32_t* l1;
-    uint32_t* lt;
     uint32_t* ln;
     uint32_t* gone;           // star: frontier neighbours lost this round
     uint32_t* cnt;
@@ -462,11 +460,9 @@ struct PatWork {
     uint32_t* cnt = nullptr;          // loop counters: blocks x n
     unsigned loop_blocks = 0;
     uint32_t* stamp1 = nullptr;       // per-round marks (round + 1)
-    uint32_t* stamp2 = nullptr;
     uint32_t* lf = nullptr;           // the round's frontier
     uint32_t* l1 = nullptr;           // alive vertices next to it
-    uint32_t* lt = nullptr;           // alive vertices within two hops of it
-    uint32_t* ln = nullptr;           // lengths of lf, l1, lt
+    uint32_t* ln = nullptr;           // lengths of lf, l1
     uint32_t* gone = nullptr;         // per vertex, zero between rounds
     unsigned long long* lvk = nullptr;   // level records on the device
     uint32_t* lvs = nullptr;
@@ -475,7 +471,7 @@ struct PatWork {
 
 void pat_free(PatWork* w, cudaStream_t s) {
     void* ptrs[] = {w->alive, w->dal, w->deg, w->core, w->stats, w->cnt,
-                    w->stamp1, w->stamp2, w->lf, w->l1, w->lt, w->ln, w->gone,
+                    w->stamp1, w->lf, w->l1, w->ln, w->gone,
                     w->lvk, w->lvs, w->lvm};
     for (void* p : ptrs) dev_free(p, s);
     *w = PatWork();
@@ -491,15 +487,12 @@ dsd_status pat_alloc(PatWork* w, uint32_t n, int pattern, cudaStream_t s) {
     DSD_TRY(dalloc(&w->lvs, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->lvm, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->stamp1, (size_t)n + 1, s));
-    DSD_TRY(dalloc(&w->stamp2, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->lf, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->l1, (size_t)n + 1, s));
-    DSD_TRY(dalloc(&w->lt, (size_t)n + 1, s));
     DSD_TRY(dalloc(&w->ln, 4, s));
     DSD_TRY(dalloc(&w->gone, (size_t)n + 1, s));
     DSD_CU(cudaMemsetAsync(w->gone, 0, ((size_t)n + 1) * 4, s));
     DSD_CU(cudaMemsetAsync(w->stamp1, 0, ((size_t)n + 1) * 4, s));
-    DSD_CU(cudaMemsetAsync(w->stamp2, 0, ((size_t)n + 1) * 4, s));
     if (pattern == kLoop && n) {
         // one counter row per block, at most ~1 GiB of rows
         uint64_t rows = (1ull << 28) / ((uint64_t)n + 1);
@@ -583,10 +576,8 @@ dsd_status decompose(dsd_graph* g, int pattern, int x, PatWork* w, Levels* L, ui
         R.lvs = w->lvs;
         R.lvm = w->lvm;
         R.stamp1 = w->stamp1;
-        R.stamp2 = w->stamp2;
         R.lf = w->lf;
         R.l1 = w->l1;
-        R.lt = w->lt;
         R.ln = w->ln;
         R.gone = w->gone;
         R.cnt = w->cnt;
