@@ -175,9 +175,10 @@ dsd_status exclusive_scan_u32_to_u64(const uint32_t* in, uint64_t* out, uint64_t
 namespace {
 
 constexpr uint32_t kSmallMax = 32;      // warp, registers
+constexpr uint32_t kWarpMax = 256;      // warp, its own 1 KB of shared memory
 constexpr uint32_t kMedMax = 2048;      // 256 threads, shared memory
 constexpr uint32_t kLargeMax = 16384;   // 1024 threads, 64 KB shared memory
-constexpr int kClasses = 4;
+constexpr int kClasses = 5;
 
 struct SortLists {
     uint32_t* rows[kClasses];
@@ -188,7 +189,7 @@ __global__ void k_classify(const uint32_t* len, uint32_t rows, SortLists L) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows;
          r += gridDim.x * blockDim.x) {
         uint32_t l = len[r];
-        int c = l <= kSmallMax ? 0 : l <= kMedMax ? 1 : l <= kLargeMax ? 2 : 3;
+        int c = l <= kSmallMax ? 0 : l <= kWarpMax ? 4 : l <= kMedMax ? 1 : l <= kLargeMax ? 2 : 3;
         uint32_t at = atomicAdd(&L.count[c], 1u);
         L.rows[c][at] = r;
     }
@@ -221,6 +222,60 @@ __global__ void k_sort_small(uint32_t* vals, const uint64_t* pos, const uint32_t
         unsigned b = __ballot_sync(0xffffffffu, keep);
         if (keep) row[__popc(b & ((1u << lane) - 1u))] = x;
         if (lane == 0) newlen[r] = __popc(b);
+    }
+}
+
+// Rows of 33..256 entries: one warp each, a bitonic network in the warp's
+// own shared-memory slice (warp synchronisation only), then the unique
+// entries written back in order.
+__global__ void __launch_bounds__(256) k_sort_warp(uint32_t* vals, const uint64_t* pos,
+                                                   const uint32_t* len, uint32_t* newlen,
+                                                   const uint32_t* list, const uint32_t* count) {
+    __shared__ uint32_t sm[8][kWarpMax];
+    const unsigned lane = lane_id();
+    uint32_t* sw = sm[threadIdx.x >> 5];
+    const uint32_t nrows = *count;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < nrows; i += nw) {
+        const uint32_t r = list[i];
+        const uint32_t l = len[r];
+        uint32_t* row = vals + pos[r];
+        uint32_t N = 64;
+        while (N < l) N <<= 1;
+        for (uint32_t j = lane; j < N; j += 32) sw[j] = j < l ? row[j] : 0xffffffffu;
+        __syncwarp();
+        for (uint32_t k = 2; k <= N; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t x = lane; x < N; x += 32) {
+                    const uint32_t y = x ^ j;
+                    if (y > x) {
+                        const bool asc = (x & k) == 0;
+                        const uint32_t a = sw[x], b = sw[y];
+                        if ((a > b) == asc) {
+                            sw[x] = b;
+                            sw[y] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        uint32_t base = 0;
+        for (uint32_t b0 = 0; b0 < l; b0 += 32) {
+            const uint32_t x = b0 + lane;
+            uint32_t v = 0;
+            bool keep = false;
+            if (x < l) {
+                v = sw[x];
+                keep = x == 0 || v != sw[x - 1];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) row[base + __popc(bal & ((1u << lane) - 1u))] = v;
+            base += __popc(bal);
+        }
+        if (lane == 0) newlen[r] = base;
+        __syncwarp();
     }
 }
 
@@ -378,6 +433,7 @@ dsd_status segmented_sort_unique(uint32_t* vals, uint32_t* tmp, const uint64_t* 
         unsigned g = (unsigned)((rows + 255) / 256);
         k_classify<<<g < 65535u ? g : 65535u, 256, 0, s>>>(len, rows, L); note_launch();
         k_sort_small<<<sms * 8, 256, 0, s>>>(vals, pos, len, newlen, L.rows[0], cnt + 0); note_launch();
+        k_sort_warp<<<sms * 8, 256, 0, s>>>(vals, pos, len, newlen, L.rows[4], cnt + 4); note_launch();
         k_sort_block<kMedMax><<<sms * 4, 256, kMedMax * 4, s>>>(vals, pos, len, newlen,
                                                                   L.rows[1], cnt + 1); note_launch();
         static bool attr_done = false;
