@@ -12,7 +12,14 @@
  *   - (k,Psi)-core decomposition (Sec. 4.3, Algorithm 3);
  *   - IncApp / CoreApp output: the (k_max,Psi)-core (Sec. 5.2, Algorithms 5
  *     and 6, Lemma 6), and the densest residual subgraph met while peeling
- *     (Sec. 5.1, Pruning1), returned as the densest nested level set R_k.
+ *     (Sec. 5.1, Pruning1), returned as the densest nested level set R_k;
+ *   - CoreExact: the exact h-clique densest subgraph by minimum cuts
+ *     (Sec. 3.1 Algorithm 1's network, Sec. 4.3 Algorithm 4);
+ *   - pattern densities for the x-star and the 4-vertex loop (Sec. 6 and
+ *     its appendix on special patterns).
+ * Not in the paper: a learned density proposal that narrows the
+ * decomposition (exact either way), a batched executor for many small
+ * graphs, and an allocation-free triangle-degree entry point.
  *
  * Conventions shared by every call:
  *   - Vertex ids are uint32 in [0, n).  Per-vertex counters are uint64.
@@ -27,8 +34,10 @@
  *     may return before the stream has finished (synchronise the stream to
  *     read them).
  *   - Errors are returned as dsd_status, never thrown; dsd_last_error()
- *     gives a message for the calling thread.  After DSD_ERR_CUDA or
- *     DSD_ERR_TIMEOUT the graph handle should be destroyed.
+ *     gives a message for the calling thread.  After DSD_ERR_CUDA the graph
+ *     handle should be destroyed; after DSD_ERR_TIMEOUT of a peel as well
+ *     (its state is partial), while a CoreExact timeout leaves the handle
+ *     usable.
  *   - A handle is not thread-safe; distinct handles are independent.
  *   - Every call computes its result entirely on the GPU; there is no CPU
  *     fallback.  Without a usable CUDA device calls return DSD_ERR_CUDA.
