@@ -484,7 +484,7 @@ def run_batched(args, local, graphs):
 
 # ------------------------------------------------------------- CPU side
 
-def cpu_sample(n, s, d, frac=0.5, seed=99):
+def cpu_sample(n, s, d, frac=0.75, seed=99):
     """Induced subgraph on a seeded random fraction of the vertices."""
     rng = np.random.default_rng(seed)
     keep = rng.random(n) < frac
@@ -516,7 +516,7 @@ def run_reference(args, rank, world):
             times.append(t)
     ms = 1e3 * float(np.mean(times))
     v = mu / (ms / 1e3)
-    sample = "induced subgraph on a seeded 50%% vertex sample (n=%d, %d draws), h=%d" % (
+    sample = "induced subgraph on a seeded 75%% vertex sample (n=%d, %d draws), h=%d" % (
         ns, ss.size, args.h)
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "h-cliques/s",
@@ -635,7 +635,7 @@ def main():
             t, smu, _ = time_oracle(ns, ss, ds, h)
             line["cpu_baseline"] = {
                 "value": smu / t, "unit": "h-cliques/s", "cores": 1, "kind": "oracle",
-                "sample": "induced subgraph on a seeded 50%% vertex sample (n=%d, %d draws), "
+                "sample": "induced subgraph on a seeded 75%% vertex sample (n=%d, %d draws), "
                           "h=%d, one run (%.1f s)" % (ns, ss.size, h, t)}
         print(json.dumps(line), flush=True)
     if world > 1:
