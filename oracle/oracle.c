@@ -1183,3 +1183,72 @@ out:
     wg_free(&g);
     return rc;
 }
+
+/* ------------------------------------------ Algorithm 2 (PeelApp) ---- */
+
+/* One clique instance through the removed vertex v (slot 0): every other
+ * member loses it (exact clique-degrees, no floor). */
+static void visit_peel_exact(lister* L, const uint32_t* c) {
+    for (int i = 1; i < L->h; i++) {
+        uint32_t u = c[i];
+        L->deg[u]--;
+        vh_up(L->heap, L->heap->pos[u]);
+    }
+}
+
+/* Algorithm 2 (PeelApp, Sec. 3.2): remove a vertex of minimum current
+ * clique-degree (ties: the smaller original id) one at a time and keep the
+ * densest of the sets met.  The sets are G itself and every residual; a
+ * later set replaces the best only when strictly denser.  in_best[v]
+ * (original ids) marks the best set; *mu_out and *size_out are its clique
+ * count and size (with no h-clique: G, 0 cliques). */
+int orc_peel_app(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
+                 uint8_t* in_best, uint64_t* mu_out, uint64_t* size_out) {
+    if (check_h(h)) return ORC_EINVAL;
+    wgraph g;
+    if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
+    lister L;
+    int rc = ORC_ENOMEM;
+    uint8_t* alive = NULL; uint32_t* tie = NULL; uint32_t* order = NULL;
+    vheap H; memset(&H, 0, sizeof(H));
+    if (lister_init(&L, &g, h, visit_count)) goto out;
+    L.deg = (uint64_t*)calloc((size_t)(n ? n : 1), sizeof(uint64_t));
+    alive = (uint8_t*)malloc((size_t)(n ? n : 1));
+    tie = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    order = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    H.heap = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    H.pos = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    if (!L.deg || !alive || !tie || !order || !H.heap || !H.pos) goto out;
+    list_all(&L);                                  /* clique-degrees and mu(G) */
+    uint64_t mu = L.mu;
+    for (uint32_t i = 0; i < n; i++) { alive[i] = 1; tie[i] = g.old_of[i]; }
+    H.key = L.deg; H.tie = tie; H.size = n;
+    for (uint32_t i = 0; i < n; i++) { H.heap[i] = i; H.pos[i] = i; }
+    for (int64_t i = (int64_t)n / 2 - 1; i >= 0; i--) vh_down(&H, (uint32_t)i);
+    L.visit = visit_peel_exact;
+    L.heap = &H;
+    uint64_t bmu = mu, bsize = n, bstep = 0, size = n, step = 0;
+    while (H.size) {
+        uint32_t v = vh_pop(&H);
+        order[step++] = v;
+        mu -= L.deg[v];                            /* the cliques through v */
+        list_containing(&L, v, alive);
+        alive[v] = 0;
+        size--;
+        if (size && (unsigned __int128)mu * bsize > (unsigned __int128)bmu * size) {
+            bmu = mu;
+            bsize = size;
+            bstep = step;
+        }
+    }
+    for (uint32_t i = 0; i < n; i++) in_best[i] = 0;
+    for (uint64_t j = bstep; j < n; j++) in_best[g.old_of[order[j]]] = 1;
+    *mu_out = bmu;
+    *size_out = bsize;
+    rc = ORC_OK;
+out:
+    free(L.deg); free(alive); free(tie); free(order);
+    free(H.heap); free(H.pos);
+    lister_free(&L); wg_free(&g);
+    return rc;
+}
