@@ -69,4 +69,10 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
     rc = lib.dsd_core_exact(None, 3, None, 0, None)
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
+    rc = lib.dsd_pattern_degrees(None, 1, 2, None, None, 0)
+    assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
+    rc = lib.dsd_pattern_core_decompose(None, 2, 0, None, None, None, None, None, 0, None, 0)
+    assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
+    rc = lib.dsd_pattern_core_app(None, 1, 3, None, None, 0, None)
+    assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
     lib.dsd_graph_destroy(None)   # NULL-safe
