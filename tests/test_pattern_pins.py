@@ -143,3 +143,60 @@ def test_pattern_core_app_densest_level(orc):
         dens = [orc.density(m, z) for m, z in zip(mu, size)]
         assert orc.density(r["densest_mu"], r["densest_size"]) == max(dens)
         assert r["kmax"] == km and r["kmax_core_mu"] == int(mu[-1])
+
+
+def _alive_degrees(A, alive):
+    return {v: len(A[v] & alive) for v in alive}
+
+
+@pytest.mark.parametrize("x", [2, 3])
+def test_star_decrements_closed_form(orc, x):
+    # appendix 1.2: removing v lowers a neighbour u by C(y-1, x-1) + C(z_u-1, x-1)
+    # (y, z_u: alive degrees before the removal) and a 2-hop vertex w reached
+    # through u by C(z_u-2, x-2) per such u; the oracle's recounts agree
+    for seed in range(6):
+        n, s, d = gg.random_small(12, 0.4, seed=1100 + seed)
+        A = _adj_sets(n, s, d)
+        g = orc.csr(n, s, d)
+        before, _ = orc.pattern_degrees(g, orc.STAR, x)
+        for v in range(n):
+            alive = np.ones(n, np.uint8)
+            alive[v] = 0
+            after, _ = orc.pattern_degrees(g, orc.STAR, x, alive)
+            z = _alive_degrees(A, set(range(n)))
+            y = z[v]
+            want = {u: 0 for u in range(n) if u != v}
+            for u in A[v]:
+                want[u] += math.comb(y - 1, x - 1) + math.comb(z[u] - 1, x - 1)
+                for w in A[u]:
+                    if w != v:
+                        want[w] += math.comb(z[u] - 2, x - 2) if z[u] >= 2 else 0
+            for u in want:
+                assert int(before[u]) - int(after[u]) == want[u], (seed, v, u)
+
+
+def test_loop_decrements_closed_form(orc):
+    # appendix 2.2: group the 2-paths v - a - w by w (y_w of them); removing v
+    # lowers w by C(y_w, 2) and each a of the group by y_w - 1
+    for seed in range(6):
+        n, s, d = gg.random_small(12, 0.45, seed=1200 + seed)
+        A = _adj_sets(n, s, d)
+        g = orc.csr(n, s, d)
+        before, _ = orc.pattern_degrees(g, orc.LOOP4)
+        for v in range(n):
+            alive = np.ones(n, np.uint8)
+            alive[v] = 0
+            after, _ = orc.pattern_degrees(g, orc.LOOP4, 0, alive)
+            want = {u: 0 for u in range(n) if u != v}
+            groups = {}
+            for a in A[v]:
+                for w in A[a]:
+                    if w != v:
+                        groups.setdefault(w, []).append(a)
+            for w, path_mids in groups.items():
+                yw = len(path_mids)
+                want[w] += math.comb(yw, 2)
+                for a in path_mids:
+                    want[a] += yw - 1
+            for u in want:
+                assert int(before[u]) - int(after[u]) == want[u], (seed, v, u)
