@@ -335,7 +335,7 @@ def run_learned(args, local):
         elif model == "topdown":
             r, info = L.dsd_core_app_topdown(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
         else:
-            r, info = L.dsd_core_app_seeded(g, h, model.handle, kc.data_ptr(), de.data_ptr(),
+            r, info = L.dsd_core_app_seeded_info(g, h, model.handle, kc.data_ptr(), de.data_ptr(),
                                             L.DSD_MEM_DEVICE)
         return g, r, info
 

@@ -61,8 +61,8 @@ typedef enum {
     DSD_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
     DSD_ERR_TIMEOUT = 4,     /* a bounded inter-block wait ran out (see dsd_set_wait_limit_ms) */
     DSD_ERR_OVERFLOW = 5,    /* a result does not fit the caller's buffer or a counter overflowed */
-    DSD_ERR_UNSUPPORTED = 6, /* input outside what the library handles (message says why) */
-    DSD_ERR_INTERNAL = 7
+    DSD_ERR_INTERNAL = 6,    /* a self-check of the library failed (message says which) */
+    DSD_ERR_UNSUPPORTED = 7  /* input outside what the library handles (message says why) */
 } dsd_status;
 
 enum { DSD_MEM_HOST = 0, DSD_MEM_DEVICE = 1 };
@@ -99,6 +99,22 @@ dsd_status dsd_set_peel_small_limit(uint32_t max_alive);
  * memory below about 4,600; the default is as large as those hold; 0 =
  * never).  Results do not depend on it.  Process-wide. */
 dsd_status dsd_set_peel_tail_limit(uint32_t max_alive);
+
+/* Checked mode (off by default; process-wide, for calls started
+ * afterwards).  Clique-degrees and mu are exact unsigned 64-bit integers;
+ * no graph this library can hold reaches 2^64 h-cliques through a vertex in
+ * practice, but in checked mode every addition into a per-vertex counter or
+ * into mu also tests for wrap-around, and a wrapped counter makes the call
+ * return DSD_ERR_OVERFLOW instead of a wrong count.  Costs a returned
+ * atomic per addition. */
+dsd_status dsd_set_checked(int on);
+/* Self-test of that checked addition on the current device: starting from
+ * `start`, adds addends[0..count) (host array, count <= 2^20) one by one
+ * into a device counter exactly as the counting kernels do in checked mode;
+ * *sum receives the (wrapped) result and *overflowed 1 if any addition
+ * wrapped, else 0. */
+dsd_status dsd_checked_add_selftest(uint64_t start, const uint64_t* addends, uint32_t count,
+                                    uint64_t* sum, int* overflowed);
 
 /* ---------------------------------------------------------------- graphs */
 
@@ -181,7 +197,10 @@ typedef struct {
     uint64_t best_k;          /* S* = R_best_k */
     uint64_t densest_mu;      /* mu(S*); rho(S*) = densest_mu / densest_size exactly */
     uint32_t nlevels;         /* number of distinct core values */
-    uint32_t reserved;
+    int32_t seeded_accepted;  /* dsd_core_app_seeded: 1 if answered from the (seed_k,Psi)-core
+                                 of the proposal, 0 if it fell back; 0 for every other call */
+    uint64_t seed_k;          /* dsd_core_app_seeded: ceil(rho') of the proposal (0 when there
+                                 was no usable proposal); 0 for every other call */
 } dsd_core_app_result;
 
 /* CoreApp / IncApp output (Algorithms 5 and 6, Lemma 6) plus Pruning1's
@@ -258,10 +277,14 @@ typedef struct {
 
 /* dsd_core_app with a proposal from model m: identical outputs (kmax_core,
  * densest, r); r->nlevels counts the levels at or above seed_k when
- * accepted.  info (may be NULL) describes what happened. */
-dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* m, uint32_t* kmax_core,
-                               uint32_t* densest, int mem, dsd_core_app_result* r,
-                               dsd_seed_info* info);
+ * accepted, r->seeded_accepted and r->seed_k say what the proposal did.
+ * The model is only read. */
+dsd_status dsd_core_app_seeded(dsd_graph* g, int h, const dsd_model* m, uint32_t* kmax_core,
+                               uint32_t* densest, int mem, dsd_core_app_result* r);
+/* The same, with the proposal's details in info (may be NULL). */
+dsd_status dsd_core_app_seeded_info(dsd_graph* g, int h, const dsd_model* m,
+                                    uint32_t* kmax_core, uint32_t* densest, int mem,
+                                    dsd_core_app_result* r, dsd_seed_info* info);
 
 /* ---------------------------------------------- CoreApp's top-down schedule */
 
@@ -374,7 +397,7 @@ dsd_status dsd_pattern_core_app(dsd_graph* g, int pattern, int x, uint32_t* kmax
  * outputs) for every graph of a batch in one persistent kernel whose CTAs
  * take graphs from a work queue (largest first), each graph handled by one
  * CTA.  The launch is captured once in a CUDA graph and replayed by
- * dsd_batch_run.
+ * dsd_batch_replay.
  *   count graphs; graph i has n[i] vertices (<= 65535), clique size h[i]
  *   (2..4) and m[i] edges: src/dst[e_i .. e_i + m[i]) with e_i the sum of
  *   the earlier m (same clean-up rules as dsd_graph_from_edges).
@@ -390,7 +413,7 @@ dsd_status dsd_batch_create(uint32_t count, const uint32_t* n, const int* h, con
                             const uint32_t* src, const uint32_t* dst, int mem, int want_cores,
                             void* cuda_stream, const char* autotune_cache, dsd_batch** out);
 /* Run the whole batch once (one graph replay; asynchronous on the stream). */
-dsd_status dsd_batch_run(dsd_batch* b);
+dsd_status dsd_batch_replay(dsd_batch* b);
 /* Results of the last run (synchronises the stream).  res: count entries
  * (the fields of dsd_core_app_result; kmax_core/densest sets are not kept);
  * status: count entries, 0 ok, 1 invalid graph, 2 unsupported (h = 4 with
@@ -402,6 +425,23 @@ dsd_status dsd_batch_info(const dsd_batch* b, uint32_t* threads, uint32_t* ctas_
                           float* tuned_ms);
 void dsd_batch_destroy(dsd_batch* b);
 
+/* CoreApp outputs (no vertex sets) for `count` existing graph handles in one
+ * call: rs[i] gets what dsd_core_app(gs[i], hs[i], ...) returns, and
+ * cores[i] (host memory, n_i entries; cores or cores[i] may be NULL) the
+ * core numbers of dsd_core_decompose.  Graphs within the batch kernel's
+ * limits (n <= 65535, 2 <= h <= 4) run together in one persistent launch,
+ * built from the handles' cleaned CSRs (a batch created, replayed once and
+ * destroyed, on the first handle's stream; the launch shape comes from
+ * autotune_cache, which may be NULL, or is timed); every other graph -- and
+ * any the batch kernel reports unsupported -- runs through the single-graph
+ * path on its own stream.  Returns after every result is in host memory.
+ * All handles must live on the current device.
+ * Errors: DSD_ERR_INVALID (count < 0, NULL arrays, a NULL handle, h out of
+ * range), and those of the calls above. */
+dsd_status dsd_batch_run(int count, dsd_graph* const* gs, const int* hs,
+                         dsd_core_app_result* rs, uint64_t* const* cores,
+                         const char* autotune_cache);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* The paper has no counterpart to this call; it exists for callers that
@@ -410,15 +450,20 @@ void dsd_batch_destroy(dsd_batch* b);
  * middle of a request).  It computes what dsd_clique_degrees computes for
  * h = 3 (triangle clique-degrees deg[v] and mu), directly from a caller CSR,
  * without a graph handle and without allocating anything.
- *   off: device pointer, n+1 entries; adj: device pointer, off[n] entries.
- *        The CSR must already be symmetric with ascending, duplicate-free
- *        rows and no self-loops (e.g. the output of dsd_graph_csr).
+ *   off: device pointer, n+1 entries; adj: device pointer, off[n] entries
+ *        (may be NULL when off[n] = 0; the call then reads off[n] back and
+ *        synchronises the stream to check it).  The CSR must already be
+ *        symmetric with ascending, duplicate-free rows and no self-loops
+ *        (e.g. the output of dsd_graph_csr).
  *   deg: device pointer, n entries (written); mu: device pointer (written).
  *   cuda_stream: the stream the work is ordered on (NULL = legacy stream).
  * Its scratch is a fixed 4 MiB __device__ array that every GPU which loads
  * the library keeps until the process exits; n must not exceed 1,048,512
  * (DSD_ERR_UNSUPPORTED otherwise).  The first call on a device looks up that
- * array's address and caches it: make it before any stream capture begins.
+ * array's address and caches it; since CUDA may load the library's device
+ * code lazily, that first call may also be what makes the driver reserve
+ * the array.  Make one warm-up call per device before any stretch of work
+ * that must not allocate, and before any stream capture begins.
  * All calls on a device share the array, so calls that overlap on the GPU
  * (other streams, other threads) race: serialise them.  Returns once the
  * work is queued; synchronise the stream before reading deg and mu. */
@@ -437,6 +482,17 @@ dsd_status dsd_triangle_degrees_noalloc(uint32_t n, const uint64_t* off, const u
 #define DSD_NPHASES 6
 dsd_status dsd_set_profiling(dsd_graph* g, int on);
 dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* launches);
+
+/* Algorithmic bytes of one h-clique listing of g (any h >= 3; the global
+ * reads do not depend on h, deeper levels stay in shared memory):
+ *   staged: the listing kernels' own model -- offsets and N+(u) read once
+ *           per vertex, N+(x) once per oriented edge (u, x), an 8-byte
+ *           read-modify-write per counter that can be credited, deg zeroed;
+ *   merge:  a sorted-list merge intersection's -- 4 (d+(u) + d+(x)) per
+ *           oriented edge, 8 (n+1) offsets, 4 m entries, 8 n counters.
+ * Either pointer may be NULL (host memory).  Runs the degeneracy order if
+ * it has not run yet. */
+dsd_status dsd_listing_bytes(dsd_graph* g, uint64_t* staged, uint64_t* merge);
 
 /* Counters of the last peeling run: which = 0 the degeneracy (h = 2) peel,
  * 1 the last (k,Psi) peel with h >= 3.  out[DSD_PEEL_STATS] receives:

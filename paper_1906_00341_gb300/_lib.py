@@ -25,8 +25,8 @@ DSD_NPHASES = 6
 PHASES = ("csr", "order_peel", "orient", "count", "peel", "extract")
 
 STATUS = {0: "DSD_OK", 1: "DSD_ERR_INVALID", 2: "DSD_ERR_NOMEM", 3: "DSD_ERR_CUDA",
-          4: "DSD_ERR_TIMEOUT", 5: "DSD_ERR_OVERFLOW", 6: "DSD_ERR_UNSUPPORTED",
-          7: "DSD_ERR_INTERNAL"}
+          4: "DSD_ERR_TIMEOUT", 5: "DSD_ERR_OVERFLOW", 6: "DSD_ERR_INTERNAL",
+          7: "DSD_ERR_UNSUPPORTED"}
 
 
 class DSDError(RuntimeError):
@@ -40,7 +40,8 @@ class CoreAppResult(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_uint64), ("kmax_core_size", ctypes.c_uint32),
                 ("densest_size", ctypes.c_uint32), ("kmax_core_mu", ctypes.c_uint64),
                 ("best_k", ctypes.c_uint64), ("densest_mu", ctypes.c_uint64),
-                ("nlevels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("nlevels", ctypes.c_uint32), ("seeded_accepted", ctypes.c_int32),
+                ("seed_k", ctypes.c_uint64)]
 
 
 class TopdownInfo(ctypes.Structure):
@@ -96,7 +97,11 @@ SIGNATURES = {
     "dsd_core_app": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult)]),
     "dsd_batch_create": (_int, [_u32, _P, _P, _P, _P, _P, _int, _int, _P, ctypes.c_char_p,
                                 ctypes.POINTER(_P)]),
-    "dsd_batch_run": (_int, [_P]),
+    "dsd_batch_replay": (_int, [_P]),
+    "dsd_set_checked": (_int, [_int]),
+    "dsd_listing_bytes": (_int, [_P, _P, _P]),
+    "dsd_checked_add_selftest": (_int, [_u64, _P, _u32, _P, _P]),
+    "dsd_batch_run": (_int, [_int, _P, _P, _P, _P, ctypes.c_char_p]),
     "dsd_batch_results": (_int, [_P, _P, _P, _P]),
     "dsd_batch_info": (_int, [_P, _P, _P, _P]),
     "dsd_batch_destroy": (None, [_P]),
@@ -114,7 +119,8 @@ SIGNATURES = {
     "dsd_model_gradient": (_int, [_P, _P, _P, _u32, ctypes.c_float, _P, _P]),
     "dsd_model_train_step": (_int, [_P, _P, _P, _u32, ctypes.c_float, ctypes.c_float, _P]),
     "dsd_graph_features": (_int, [_P, _int, _P, _int]),
-    "dsd_core_app_seeded": (_int, [_P, _int, _P, _P, _P, _int, ctypes.POINTER(CoreAppResult),
+    "dsd_core_app_seeded": (_int, [_P, _int, _P, _P, _P, _int, ctypes.POINTER(CoreAppResult)]),
+    "dsd_core_app_seeded_info": (_int, [_P, _int, _P, _P, _P, _int, ctypes.POINTER(CoreAppResult),
                                    ctypes.POINTER(SeedInfo)]),
     "dsd_core_app_topdown": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(CoreAppResult),
                                     ctypes.POINTER(TopdownInfo)]),
@@ -177,6 +183,26 @@ def dsd_kernel_launches():
 
 def dsd_set_wait_limit_ms(ms):
     _check(load().dsd_set_wait_limit_ms(ms))
+
+
+def dsd_listing_bytes(g):
+    a = _u64()
+    b = _u64()
+    _check(load().dsd_listing_bytes(g, ctypes.addressof(a), ctypes.addressof(b)))
+    return int(a.value), int(b.value)
+
+
+def dsd_set_checked(on):
+    _check(load().dsd_set_checked(1 if on else 0))
+
+
+def dsd_checked_add_selftest(start, addends):
+    a = np.ascontiguousarray(np.asarray(addends, np.uint64))
+    out = _u64()
+    flag = ctypes.c_int()
+    _check(load().dsd_checked_add_selftest(int(start), _np_ptr(a) if a.size else 0, a.size,
+                                           ctypes.addressof(out), ctypes.addressof(flag)))
+    return int(out.value), bool(flag.value)
 
 
 def dsd_set_peel_small_limit(max_alive):
@@ -249,8 +275,38 @@ def dsd_batch_create(count, n_ptr, h_ptr, m_ptr, src_ptr, dst_ptr, mem, want_cor
     return out.value
 
 
-def dsd_batch_run(b):
-    _check(load().dsd_batch_run(b))
+def dsd_batch_replay(b):
+    _check(load().dsd_batch_replay(b))
+
+
+def dsd_batch_run(graphs, hs, want_cores=False, autotune_cache=None):
+    """CoreApp results (and core numbers when want_cores) for a list of
+    graph handles (ints or Graph objects) with clique sizes hs."""
+    count = len(graphs)
+    hv = (ctypes.c_int * max(count, 1))(*[int(h) for h in hs])
+    gv = (ctypes.c_void_p * max(count, 1))(*[int(getattr(g, "handle", g)) for g in graphs])
+    res = (CoreAppResult * max(count, 1))()
+    cores = None
+    cptr = 0
+    if want_cores:
+        ns = [dsd_graph_info(int(getattr(g, "handle", g)))[0] for g in graphs]
+        cores = [np.zeros(max(n, 1), np.uint64) for n in ns]
+        cp = (ctypes.c_void_p * max(count, 1))(*[c.ctypes.data for c in cores])
+        cptr = ctypes.addressof(cp)
+    cache = autotune_cache.encode() if autotune_cache else None
+    _check(load().dsd_batch_run(count, ctypes.addressof(gv), ctypes.addressof(hv),
+                                ctypes.addressof(res), cptr, cache))
+    out = []
+    for i in range(count):
+        r = res[i]
+        d = dict(kmax=int(r.kmax), kmax_core_size=int(r.kmax_core_size),
+                 kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
+                 densest_size=int(r.densest_size), densest_mu=int(r.densest_mu),
+                 nlevels=int(r.nlevels))
+        if cores is not None:
+            d["core"] = cores[i][: ns[i]]
+        out.append(d)
+    return out
 
 
 def dsd_batch_results(b, res_ptr, status_ptr, cores_ptr):
@@ -290,7 +346,7 @@ class Batch:
                                        1 if want_cores else 0, sp, autotune_cache)
 
     def run(self):
-        dsd_batch_run(self.handle)
+        dsd_batch_replay(self.handle)
 
     def results(self):
         res = (CoreAppResult * max(self.count, 1))()
@@ -394,9 +450,15 @@ def dsd_graph_features(g, h, f_ptr, mem):
 
 def dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem):
     r = CoreAppResult()
+    _check(load().dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem, ctypes.byref(r)))
+    return r
+
+
+def dsd_core_app_seeded_info(g, h, model, kcore_ptr, densest_ptr, mem):
+    r = CoreAppResult()
     info = SeedInfo()
-    _check(load().dsd_core_app_seeded(g, h, model, kcore_ptr, densest_ptr, mem, ctypes.byref(r),
-                                      ctypes.byref(info)))
+    _check(load().dsd_core_app_seeded_info(g, h, model, kcore_ptr, densest_ptr, mem,
+                                           ctypes.byref(r), ctypes.byref(info)))
     return r, info
 
 
@@ -645,11 +707,13 @@ class Graph:
     def core_app_seeded(self, h, model, mem="host", sets=True):
         kc = self._alloc(self.n, 4, mem) if sets else None
         de = self._alloc(self.n, 4, mem) if sets else None
-        r, info = dsd_core_app_seeded(self.handle, h, model.handle, self._ptr(kc) if sets else 0,
-                                      self._ptr(de) if sets else 0, self._memc(mem))
+        r, info = dsd_core_app_seeded_info(self.handle, h, model.handle,
+                                           self._ptr(kc) if sets else 0,
+                                           self._ptr(de) if sets else 0, self._memc(mem))
         out = dict(kmax=int(r.kmax), kmax_core_mu=int(r.kmax_core_mu), best_k=int(r.best_k),
                    densest_mu=int(r.densest_mu), densest_size=int(r.densest_size),
-                   kmax_core_size=int(r.kmax_core_size), nlevels=int(r.nlevels))
+                   kmax_core_size=int(r.kmax_core_size), nlevels=int(r.nlevels),
+                   seeded_accepted=int(r.seeded_accepted), seed_k=int(r.seed_k))
         if sets:
             out["kmax_core"] = kc[: r.kmax_core_size]
             out["densest"] = de[: r.densest_size]

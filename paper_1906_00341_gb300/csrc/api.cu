@@ -18,6 +18,9 @@ uint32_t peel_small_limit() { return g_small_limit.load(); }
 static std::atomic<uint32_t> g_tail_limit{1u << 30};
 uint32_t peel_tail_limit() { return g_tail_limit.load(); }
 
+static std::atomic<int> g_checked{0};
+bool checked_mode() { return g_checked.load() != 0; }
+
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -358,6 +361,21 @@ dsd_status dsd_set_peel_tail_limit(uint32_t max_alive) {
     return DSD_OK;
 }
 
+dsd_status dsd_set_checked(int on) {
+    g_checked = on ? 1 : 0;
+    return DSD_OK;
+}
+
+dsd_status dsd_checked_add_selftest(uint64_t start, const uint64_t* addends, uint32_t count,
+                                    uint64_t* sum, int* overflowed) {
+    set_error("");
+    if ((count && !addends) || !sum || !overflowed || count > (1u << 20)) {
+        set_error("invalid argument to dsd_checked_add_selftest");
+        return DSD_ERR_INVALID;
+    }
+    return checked_add_selftest(start, addends, count, sum, overflowed);
+}
+
 dsd_status dsd_graph_from_edges(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
                                 int mem, void* cuda_stream, dsd_graph** out) {
     set_error("");
@@ -667,7 +685,8 @@ dsd_status dsd_core_app(dsd_graph* g, int h, uint32_t* kmax_core, uint32_t* dens
     r->densest_size = hr.densest_size;
     r->densest_mu = hr.densest_mu;
     r->nlevels = hr.nlevels;
-    r->reserved = 0;
+    r->seeded_accepted = 0;
+    r->seed_k = 0;
     return DSD_OK;
 }
 
@@ -702,11 +721,17 @@ dsd_status dsd_phase_stats(dsd_graph* g, float* ms, uint64_t* bytes, uint32_t* l
         if (bytes) bytes[p] = g->prof_bytes[p];
         if (launches) launches[p] = g->prof_launches[p];
     }
-    if (g->profiling && g->last_h == 3 && bytes) {
+    if (g->profiling && g->last_h >= 3 && bytes) {
         uint64_t b = 0;
-        if (count_bytes_h3(g, &b) == DSD_OK) bytes[kPhaseCount] = g->prof_bytes[kPhaseCount] = b;
+        if (count_bytes(g, &b, nullptr) == DSD_OK)
+            bytes[kPhaseCount] = g->prof_bytes[kPhaseCount] = b;
     }
     return DSD_OK;
+}
+
+dsd_status dsd_listing_bytes(dsd_graph* g, uint64_t* staged, uint64_t* merge) {
+    DSD_TRY(check_graph(g));
+    return count_bytes(g, staged, merge);
 }
 
 }  // extern "C"

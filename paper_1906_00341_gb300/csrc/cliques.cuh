@@ -55,49 +55,129 @@ __device__ __forceinline__ void warp_build_rows32(const uint32_t* C, uint32_t nc
 }
 
 // ---------------------------------------------------------------------------
+// Per-candidate credits.  An r-clique listed as positions j1 < ... < jr of C
+// adds one to each member's counter.  The last member of a clique is one bit
+// of the leaf mask P & rows[j_{r-1}], so it is credited through bit-sliced
+// counters held in registers: 32 counters of kSlices bits, counter b being
+// bit b of S[0..kSlices-1] (S[0] least significant); adding a mask adds one
+// to every counter whose bit is set, by ripple carry.  The counters are
+// flushed (one shared-memory atomic per non-zero counter) before any of them
+// can reach 2^kSlices.  The other members are credited once per search node
+// with the number of cliques below it, instead of once per clique.
+constexpr int kSlices = 8;
+constexpr uint32_t kSliceAdds = (1u << kSlices) - 1;   // adds between flushes
+
+struct BitSliced {
+    uint32_t S[kSlices];
+    uint32_t adds;
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < kSlices; i++) S[i] = 0;
+        adds = 0;
+    }
+    __device__ __forceinline__ void add(uint32_t m) {
+        uint32_t carry = m;
+#pragma unroll
+        for (int i = 0; i < kSlices; i++) {
+            uint32_t t = S[i] & carry;
+            S[i] ^= carry;
+            carry = t;
+            if (!carry) break;
+        }
+        adds++;
+    }
+    // cnt[b] += counter b for every b; then zero.
+    template <class T>
+    __device__ __forceinline__ void flush(T* cnt) {
+        uint32_t any = 0;
+#pragma unroll
+        for (int i = 0; i < kSlices; i++) any |= S[i];
+        while (any) {
+            int b = __ffs(any) - 1;
+            any &= any - 1;
+            uint32_t v = 0;
+#pragma unroll
+            for (int i = 0; i < kSlices; i++) v |= ((S[i] >> b) & 1u) << i;
+            atomicAdd(&cnt[b], (T)v);
+        }
+        clear();
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Warp DFS over one-word rows: lane i takes the cliques whose first member
 // is candidate i.  Counts r-cliques (r >= 2) in G[C]; adds per-candidate
 // counts into cnt[] (shared memory) and returns the warp total (all lanes).
+// A node at depth d has chosen d members (sel[1..d]); P[d] holds the
+// candidates adjacent to all of them.  Nodes at depth r - 2 enumerate their
+// leaves in one loop.
 __device__ __forceinline__ unsigned long long warp_dfs32(const uint32_t* rows, uint32_t nc,
                                                         int r, unsigned* cnt) {
     unsigned lane = lane_id();
     unsigned long long total = 0;
     if (lane < nc) {
-        uint32_t P[kMaxDepth], rem[kMaxDepth];
-        uint32_t sel[kMaxDepth];
-        int depth = 1;
-        P[1] = rows[lane];
-        rem[1] = P[1];
-        sel[1] = lane;
-        // need r - 1 more members after the first
-        if (__popc(P[1]) >= r - 1) {
+        BitSliced bs;
+        bs.clear();
+        if (r == 2) {
+            uint32_t last = rows[lane];
+            unsigned c = __popc(last);
+            if (c) {
+                bs.add(last);
+                atomicAdd(&cnt[lane], c);
+                total = c;
+            }
+        } else {
+            uint32_t P[kMaxDepth], rem[kMaxDepth], sel[kMaxDepth];
+            unsigned acc[kMaxDepth];
+            int depth = 1;
+            P[1] = rows[lane];
+            rem[1] = P[1];
+            sel[1] = lane;
+            acc[1] = 0;
+            // need r - 1 more members after the first
+            if (__popc(P[1]) < r - 1) depth = 0;
             while (depth >= 1) {
-                if (depth == r - 1) {
-                    uint32_t last = P[depth];
-                    unsigned c = __popc(last);
-                    if (c) {
-                        total += c;
-                        for (int d = 1; d <= depth; d++) atomicAdd(&cnt[sel[d]], c);
-                        while (last) {
-                            int b = __ffs(last) - 1;
-                            last &= last - 1;
-                            atomicAdd(&cnt[b], 1u);
+                if (depth == r - 2) {
+                    // every j left in rem is member r-1, its leaf mask the last members
+                    uint32_t rm = rem[depth], Pd = P[depth];
+                    unsigned sub = 0;
+                    while (rm) {
+                        int j = __ffs(rm) - 1;
+                        rm &= rm - 1;
+                        uint32_t last = Pd & rows[j];
+                        unsigned c = __popc(last);
+                        if (c) {
+                            bs.add(last);
+                            if (bs.adds == kSliceAdds) bs.flush(cnt);
+                            atomicAdd(&cnt[j], c);
+                            sub += c;
                         }
                     }
-                    depth--;
+                    acc[depth] += sub;
+                } else if (rem[depth]) {
+                    int j = __ffs(rem[depth]) - 1;
+                    rem[depth] &= rem[depth] - 1;
+                    uint32_t pn = P[depth] & rows[j];
+                    if (__popc(pn) >= r - depth - 1) {
+                        depth++;
+                        sel[depth] = j;
+                        P[depth] = pn;
+                        rem[depth] = pn;
+                        acc[depth] = 0;
+                    }
                     continue;
                 }
-                if (rem[depth] == 0) { depth--; continue; }
-                int j = __ffs(rem[depth]) - 1;
-                rem[depth] &= rem[depth] - 1;
-                uint32_t pn = P[depth] & rows[j];
-                if (__popc(pn) < r - depth - 1) continue;
-                depth++;
-                sel[depth] = j;
-                P[depth] = pn;
-                rem[depth] = pn;
+                // leave the node: credit its member with the cliques below it
+                unsigned a = acc[depth];
+                if (a) {
+                    atomicAdd(&cnt[sel[depth]], a);
+                    if (depth > 1) acc[depth - 1] += a;
+                    else total = a;
+                }
+                depth--;
             }
         }
+        bs.flush(cnt);
     }
     return warp_sum(total);
 }
@@ -123,59 +203,98 @@ __device__ __forceinline__ void block_build_rows(const uint32_t* C, uint32_t nc,
     }
 }
 
-// Warps take first members i; lane l holds word l of the current sets.
-// Returns this thread's share of the total (sum over the block = total).
+// Warps take first members i from the shared counter *next_i (zero on
+// entry; the early candidates, with the largest searches below them, go
+// first); lane l holds word l of the current sets (and the bit-sliced
+// counters of candidates 32 l .. 32 l + 31).  Returns this thread's share of
+// the total (sum over the block = total).
 __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, uint32_t nc,
                                                        uint32_t W, int r,
-                                                       unsigned long long* cnt) {
+                                                       unsigned long long* cnt,
+                                                       uint32_t* next_i) {
+    const unsigned full = 0xffffffffu;
     unsigned lane = lane_id();
-    unsigned nw = blockDim.x >> 5;
     unsigned long long total = 0;
-    for (uint32_t i = warp_id(); i < nc; i += nw) {
+    BitSliced bs;
+    bs.clear();
+    for (;;) {
+        uint32_t i = 0;
+        if (lane == 0) i = atomicAdd(next_i, 1u);
+        i = __shfl_sync(full, i, 0);
+        if (i >= nc) break;
         uint32_t P[kMaxDepth], rem[kMaxDepth];
         uint32_t sel[kMaxDepth];
+        unsigned long long acc[kMaxDepth];
         int depth = 1;
         P[1] = lane < W ? rows[i * W + lane] : 0u;
         rem[1] = P[1];
         sel[1] = i;
-        int pc = __reduce_add_sync(0xffffffffu, (unsigned)__popc(P[1]));
-        if (pc < r - 1) continue;
+        acc[1] = 0;
+        unsigned pc = __reduce_add_sync(full, (unsigned)__popc(P[1]));
+        if ((int)pc < r - 1) continue;
+        if (r == 2) {
+            bs.add(P[1]);
+            if (bs.adds == kSliceAdds) bs.flush(cnt + lane * 32);
+            if (lane == 0) {
+                atomicAdd(&cnt[i], (unsigned long long)pc);
+                total += pc;
+            }
+            continue;
+        }
         while (depth >= 1) {
-            if (depth == r - 1) {
-                uint32_t last = P[depth];
-                unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(last));
-                if (c) {
-                    if (lane == 0) {
-                        total += c;
-                        for (int d = 1; d <= depth; d++)
-                            atomicAdd(&cnt[sel[d]], (unsigned long long)c);
-                    }
-                    while (last) {
-                        int b = __ffs(last) - 1;
-                        last &= last - 1;
-                        atomicAdd(&cnt[lane * 32 + b], 1ull);
+            if (depth == r - 2) {
+                // every j left in rem is member r-1, its leaf mask the last members
+                const uint32_t Pd = P[depth];
+                uint32_t rm = rem[depth];
+                unsigned long long sub = 0;
+                for (;;) {
+                    unsigned have = __ballot_sync(full, rm != 0);
+                    if (!have) break;
+                    int fl = __ffs(have) - 1;
+                    uint32_t word = __shfl_sync(full, rm, fl);
+                    uint32_t j = (uint32_t)fl * 32 + (__ffs(word) - 1);
+                    if ((int)lane == fl) rm &= rm - 1;
+                    uint32_t last = Pd & (lane < W ? rows[j * W + lane] : 0u);
+                    unsigned c = __reduce_add_sync(full, (unsigned)__popc(last));
+                    if (c) {
+                        bs.add(last);
+                        if (bs.adds == kSliceAdds) bs.flush(cnt + lane * 32);
+                        if (lane == 0) atomicAdd(&cnt[j], (unsigned long long)c);
+                        sub += c;
                     }
                 }
-                depth--;
-                continue;
+                acc[depth] += sub;
+            } else {
+                unsigned have = __ballot_sync(full, rem[depth] != 0);
+                if (have) {
+                    int fl = __ffs(have) - 1;
+                    uint32_t word = __shfl_sync(full, rem[depth], fl);
+                    uint32_t j = (uint32_t)fl * 32 + (__ffs(word) - 1);
+                    if ((int)lane == fl) rem[depth] &= rem[depth] - 1;
+                    uint32_t pn = P[depth] & (lane < W ? rows[j * W + lane] : 0u);
+                    int c = (int)__reduce_add_sync(full, (unsigned)__popc(pn));
+                    if (c >= r - depth - 1) {
+                        depth++;
+                        sel[depth] = j;
+                        P[depth] = pn;
+                        rem[depth] = pn;
+                        acc[depth] = 0;
+                    }
+                    continue;
+                }
             }
-            unsigned have = __ballot_sync(0xffffffffu, rem[depth] != 0);
-            if (!have) { depth--; continue; }
-            int fl = __ffs(have) - 1;
-            uint32_t word = __shfl_sync(0xffffffffu, rem[depth], fl);
-            int bit = __ffs(word) - 1;
-            uint32_t j = (uint32_t)fl * 32 + bit;
-            if ((int)lane == fl) rem[depth] &= rem[depth] - 1;
-            uint32_t pn = P[depth] & (lane < W ? rows[j * W + lane] : 0u);
-            int c = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pn));
-            if (c < r - depth - 1) continue;
-            depth++;
-            sel[depth] = j;
-            P[depth] = pn;
-            rem[depth] = pn;
+            // leave the node: credit its member with the cliques below it
+            unsigned long long a = acc[depth];
+            if (a) {
+                if (lane == 0) atomicAdd(&cnt[sel[depth]], a);
+                if (depth > 1) acc[depth - 1] += a;
+                else total += a;
+            }
+            depth--;
         }
     }
-    return total;
+    bs.flush(cnt + lane * 32);
+    return lane == 0 ? total : 0ull;
 }
 
 }  // namespace dsd

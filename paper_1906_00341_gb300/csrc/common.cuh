@@ -94,6 +94,19 @@ __device__ __forceinline__ uint64_t lower_bound_u32(P a, uint64_t len, uint32_t 
     return lo;
 }
 
+// Checked mode (dsd_set_checked): an addition into a 64-bit counter that
+// wraps around sets *ovf instead of passing silently (ovf null: unchecked).
+bool checked_mode();
+__device__ __forceinline__ void add_counter(unsigned long long* p, unsigned long long v,
+                                            uint32_t* ovf) {
+    if (ovf) {
+        unsigned long long old = atomicAdd(p, v);
+        if (old + v < old) atomicOr(ovf, 1u);
+    } else {
+        atomicAdd(p, v);
+    }
+}
+
 // u64 atomic subtract returning the old value.
 __device__ __forceinline__ unsigned long long atomic_sub_u64(unsigned long long* p,
                                                             unsigned long long v) {

@@ -31,8 +31,9 @@ struct CountArgs {
     unsigned long long* mu;
     uint32_t* listM;      // vertices of tier M
     uint32_t* listL;      // vertices of tier L
-    uint32_t* cntML;      // [2]
+    uint32_t* cntML;      // [0] tier M, [1] tier L, [2] unsupported vertices
     uint32_t* work;       // [1] dynamic queue for tier S
+    uint32_t* ovf;        // checked mode: set when a counter wraps (else null)
 };
 
 // Tier S + classification.  One warp per vertex.
@@ -94,25 +95,29 @@ __global__ void __launch_bounds__(kCountThreads) k_count_small(CountArgs A) {
             }
             __syncwarp();
             if (tot) {
-                if (lane < d && cnt[lane]) atomicAdd(&A.deg[C[lane]], (unsigned long long)cnt[lane]);
+                if (lane < d && cnt[lane])
+                    add_counter(&A.deg[C[lane]], (unsigned long long)cnt[lane], A.ovf);
                 if (lane == 0) {
-                    atomicAdd(&A.deg[u], tot);
+                    add_counter(&A.deg[u], tot, A.ovf);
+                    if (A.ovf && mu_acc + tot < mu_acc) atomicOr(A.ovf, 1u);
                     mu_acc += tot;
                 }
             }
             __syncwarp();
         }
     }
-    if (lane == 0 && mu_acc) atomicAdd(A.mu, mu_acc);
+    if (lane == 0 && mu_acc) add_counter(A.mu, mu_acc, A.ovf);
 }
 
 // Tier M: one block per vertex, |N+(u)| in (32, 1024].
-__global__ void __launch_bounds__(kCountThreads) k_count_medium(CountArgs A) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_count_medium(CountArgs A) {
     extern __shared__ uint32_t smem[];
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // 1024
     uint32_t* C = smem + 2 * kBitmapMax;      // 1024
     uint32_t* rows = smem + 3 * kBitmapMax;   // up to 1024*32 (only if r >= 3)
     __shared__ unsigned long long s_tot;
+    __shared__ uint32_t s_next;
     uint32_t nM = A.cntML[0];
     for (uint32_t it = blockIdx.x; it < nM; it += gridDim.x) {
         uint32_t u = A.listM[it];
@@ -122,7 +127,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count_medium(CountArgs A) {
         for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) { C[i] = A.adj[b + i]; cnt[i] = 0; }
         if (A.r >= 3)
             for (uint32_t i = threadIdx.x; i < d * W; i += blockDim.x) rows[i] = 0;
-        if (threadIdx.x == 0) s_tot = 0;
+        if (threadIdx.x == 0) {
+            s_tot = 0;
+            s_next = 0;
+        }
         __syncthreads();
         unsigned long long mine = 0;
         if (A.r == 2) {
@@ -143,17 +151,17 @@ __global__ void __launch_bounds__(kCountThreads) k_count_medium(CountArgs A) {
         } else {
             block_build_rows(C, d, W, A.off + 1, A.adj, A.split, rows);
             __syncthreads();
-            mine = block_dfs(rows, d, W, A.r, cnt);
+            mine = block_dfs(rows, d, W, A.r, cnt, &s_next);
         }
         if (mine) atomicAdd(&s_tot, mine);
         __syncthreads();
         unsigned long long tot = s_tot;
         if (tot) {
             for (uint32_t i = threadIdx.x; i < d; i += blockDim.x)
-                if (cnt[i]) atomicAdd(&A.deg[C[i]], cnt[i]);
+                if (cnt[i]) add_counter(&A.deg[C[i]], cnt[i], A.ovf);
             if (threadIdx.x == 0) {
-                atomicAdd(&A.deg[u], tot);
-                atomicAdd(A.mu, tot);
+                add_counter(&A.deg[u], tot, A.ovf);
+                add_counter(A.mu, tot, A.ovf);
             }
         }
         __syncthreads();
@@ -181,16 +189,19 @@ __global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
             for (uint64_t p = xb + lane; p < xe; p += 32) {
                 uint32_t y = A.adj[p];
                 uint64_t pos = lower_bound_u32(C, d, y);
-                if (pos < d && C[pos] == y) { atomicAdd(&A.deg[y], 1ull); hits++; }
+                if (pos < d && C[pos] == y) { add_counter(&A.deg[y], 1ull, A.ovf); hits++; }
             }
             hits = __reduce_add_sync(0xffffffffu, hits);
-            if (lane == 0 && hits) { atomicAdd(&A.deg[x], (unsigned long long)hits); mine += hits; }
+            if (lane == 0 && hits) {
+                add_counter(&A.deg[x], (unsigned long long)hits, A.ovf);
+                mine += hits;
+            }
         }
         if (mine) atomicAdd(&s_tot, mine);
         __syncthreads();
         if (threadIdx.x == 0 && s_tot) {
-            atomicAdd(&A.deg[u], s_tot);
-            atomicAdd(A.mu, s_tot);
+            add_counter(&A.deg[u], s_tot, A.ovf);
+            add_counter(A.mu, s_tot, A.ovf);
         }
         __syncthreads();
     }
@@ -201,24 +212,37 @@ __global__ void k_degree_as_count(uint32_t n, const uint64_t* off, unsigned long
         deg[v] = off[v + 1] - off[v];
 }
 
-// Algorithmic bytes of the h = 3 listing (documented model): offsets and
-// split read once per vertex, each N+(u) read once, each N+(x) read once per
-// oriented edge (u, x), one 8-byte read-modify-write per credited counter.
-__global__ void k_count_bytes3(uint32_t n, const uint64_t* off, const uint32_t* adj,
-                               const uint64_t* split, unsigned long long* out) {
-    unsigned long long acc = 0;
+// Algorithmic bytes of the listing, two models (per launch of the count):
+// out[0], the kernels' own staging: offsets and split read once per vertex,
+// each N+(u) read once (it is staged in shared memory), each N+(x) read once
+// per oriented edge (u, x), one 8-byte read-modify-write per counter that
+// can be credited (u and every x), the 8-byte zero-fill of deg;
+// out[1], a merge intersection's: both lists of every oriented edge,
+// 4 (d+(u) + d+(x)), plus 8 (n+1) offsets, 4 m oriented entries and the
+// 8 n counters written.  Bitmap searches below the first level (h >= 4)
+// stay in shared memory and are in neither.
+__global__ void k_count_bytes(uint32_t n, const uint64_t* off, const uint32_t* adj,
+                              const uint64_t* split, unsigned long long* out) {
+    unsigned long long acc = 0, mrg = 0;
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         uint64_t b = split[u], e = off[u + 1];
         acc += 16 + 4 * (e - b);              // off + split, N+(u)
         for (uint64_t p = b; p < e; p++) {
             uint32_t x = adj[p];
-            acc += 16 + 4 * (off[x + 1] - split[x]);   // off/split of x, N+(x)
-            acc += 16;                                  // counter of x
+            uint64_t dx = off[x + 1] - split[x];
+            acc += 16 + 4 * dx;               // off/split of x, N+(x)
+            acc += 16;                        // counter of x
+            mrg += 4 * ((e - b) + dx);
         }
-        acc += 16;                                      // counter of u
+        acc += 16 + 8;                        // counter of u, its zero-fill
+        mrg += 8 + 4 * (e - b) + 8;
     }
     acc = warp_sum(acc);
-    if (lane_id() == 0) atomicAdd(out, acc);
+    mrg = warp_sum(mrg);
+    if (lane_id() == 0) {
+        atomicAdd(out, acc);
+        atomicAdd(out + 1, mrg);
+    }
 }
 
 }  // namespace
@@ -254,23 +278,34 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     A.listL = ws + n;
     A.cntML = ws + 2 * (size_t)n;
     A.work = A.cntML + 4;
+    A.ovf = checked_mode() ? A.cntML + 3 : nullptr;
     dsd_status st = DSD_OK;
     cudaError_t e = cudaMemsetAsync(A.cntML, 0, 8 * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         k_count_small<<<sms * 8, kCountThreads, 0, s>>>(A); note_launch();
         size_t smemM = (size_t)3 * kBitmapMax * 4 + (h >= 4 ? (size_t)kBitmapMax * 32 * 4 : 0);
-        if (smemM > 48 * 1024)
-            cudaFuncSetAttribute(k_count_medium, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smemM);
-        k_count_medium<<<sms * (h >= 4 ? 1 : 4), kCountThreads, smemM, s>>>(A); note_launch();
+        if (h >= 4) {
+            // one block per SM (the rows fill its shared memory): 32 warps
+            cudaFuncSetAttribute(k_count_medium<1024>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemM);
+            k_count_medium<1024><<<sms, 1024, smemM, s>>>(A);
+        } else {
+            k_count_medium<kCountThreads><<<sms * 4, kCountThreads, smemM, s>>>(A);
+        }
+        note_launch();
         if (h == 3) k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A); note_launch();
         e = cudaGetLastError();
     }
-    uint32_t unsupported = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&unsupported, A.cntML + 2, 4, cudaMemcpyDeviceToHost, s);
+    uint32_t flags[2] = {0, 0};   // unsupported vertices, counter overflow
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags, A.cntML + 2, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "clique count", __FILE__, __LINE__);
+    const uint32_t unsupported = flags[0];
+    if (flags[1]) {
+        set_error("h=%d: a clique-degree or mu exceeds 2^64 - 1 (checked mode)", h);
+        return DSD_ERR_OVERFLOW;
+    }
     if (unsupported) {
         set_error("h=%d listing needs at most %u higher-ranked neighbours per vertex; %u vertices "
                   "exceed it (degeneracy %u)", h, kBitmapMax, unsupported, g->degeneracy);
@@ -280,20 +315,57 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     return st;
 }
 
-dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out) {
+namespace {
+// Adds addends[0..count) one after another into a counter starting at
+// start, through the checked addition of the counting kernels.
+__global__ void k_checked_add_probe(unsigned long long start, const unsigned long long* addends,
+                                    uint32_t count, unsigned long long* out, uint32_t* ovf) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    *out = start;
+    for (uint32_t i = 0; i < count; i++) add_counter(out, addends[i], ovf);
+}
+}  // namespace
+
+dsd_status checked_add_selftest(uint64_t start, const uint64_t* addends, uint32_t count,
+                                uint64_t* sum, int* overflowed) {
+    unsigned long long* d = nullptr;
+    DSD_TRY(dalloc(&d, (size_t)count + 2, nullptr));
+    uint32_t* ovf = reinterpret_cast<uint32_t*>(d + count + 1);
+    cudaError_t e = cudaMemset(ovf, 0, 4);
+    if (e == cudaSuccess && count)
+        e = cudaMemcpy(d, addends, (size_t)count * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_checked_add_probe<<<1, 32>>>(start, d, count, d + count, ovf);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    unsigned long long out = 0;
+    uint32_t flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&out, d + count, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, ovf, 4, cudaMemcpyDeviceToHost);
+    dev_free(d, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "checked add self-test", __FILE__, __LINE__);
+    *sum = out;
+    *overflowed = flag ? 1 : 0;
+    return DSD_OK;
+}
+
+dsd_status count_bytes(dsd_graph* g, uint64_t* staged, uint64_t* merge) {
+    DSD_TRY(ensure_order(g));
     cudaStream_t s = g->stream;
     unsigned long long* d = nullptr;
-    DSD_TRY(dalloc(&d, 1, s));
-    DSD_CU(cudaMemsetAsync(d, 0, 8, s));
+    DSD_TRY(dalloc(&d, 2, s));
+    DSD_CU(cudaMemsetAsync(d, 0, 16, s));
     int sms = 152;
     num_sms(&sms);
-    k_count_bytes3<<<sms * 8, 256, 0, s>>>(g->n, g->roff, g->radj, g->rsplit, d); note_launch();
-    unsigned long long h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s);
+    k_count_bytes<<<sms * 8, 256, 0, s>>>(g->n, g->roff, g->radj, g->rsplit, d); note_launch();
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(d, s);
     if (e != cudaSuccess) return cuda_fail(e, "count bytes", __FILE__, __LINE__);
-    *out = h + 8ull * g->n;   // + mu/counters initialisation is not counted; deg zero-fill
+    if (staged) *staged = h[0];
+    if (merge) *merge = h[1] + 8;   // the final offset
     return DSD_OK;
 }
 

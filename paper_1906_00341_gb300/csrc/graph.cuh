@@ -73,7 +73,12 @@ dsd_status ensure_order(dsd_graph* g);
 // h-clique counting on the relabelled graph: deg_new[rank] and *mu_dev (device pointers).
 dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
                          unsigned long long* mu_dev);
-dsd_status count_bytes_h3(dsd_graph* g, uint64_t* out);
+// Algorithmic bytes of one listing under the kernels' staging model and
+// under a merge-intersection model (k_count_bytes).
+dsd_status count_bytes(dsd_graph* g, uint64_t* staged, uint64_t* merge);
+// The counting kernels' checked addition on given values (dsd_checked_add_selftest).
+dsd_status checked_add_selftest(uint64_t start, const uint64_t* addends, uint32_t count,
+                                uint64_t* sum, int* overflowed);
 
 // Level-synchronous (k,Psi)-core peeling.
 struct PeelResult {

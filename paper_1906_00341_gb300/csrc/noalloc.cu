@@ -167,8 +167,8 @@ extern "C" dsd_status dsd_triangle_degrees_noalloc(uint32_t n, const uint64_t* o
                                                    const uint32_t* adj, uint64_t* deg,
                                                    uint64_t* mu, void* cuda_stream) {
     set_error("");
-    if (!off || !deg || !mu || (n && !adj)) {
-        set_error("dsd_triangle_degrees_noalloc: off, adj, deg and mu must be device pointers");
+    if (!off || !deg || !mu) {
+        set_error("dsd_triangle_degrees_noalloc: off, deg and mu must be device pointers");
         return DSD_ERR_INVALID;
     }
     if (n > kNoAllocMaxN) {
@@ -176,9 +176,21 @@ extern "C" dsd_status dsd_triangle_degrees_noalloc(uint32_t n, const uint64_t* o
                   "scratch is a fixed %u-word device array", kNoAllocMaxN, n, kNoAllocWords);
         return DSD_ERR_UNSUPPORTED;
     }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (n && !adj) {
+        // an edgeless CSR may come with a null adj (a zero-length device
+        // buffer has no address); any other null adj is an error
+        uint64_t edges = 0;
+        DSD_CU(cudaMemcpyAsync(&edges, off + n, sizeof(edges), cudaMemcpyDeviceToHost, s));
+        DSD_CU(cudaStreamSynchronize(s));
+        if (edges) {
+            set_error("dsd_triangle_degrees_noalloc: adj is NULL but off[n] = %llu",
+                      (unsigned long long)edges);
+            return DSD_ERR_INVALID;
+        }
+    }
     uint32_t* scratch = nullptr;
     DSD_TRY(scratch_for_current_device(&scratch));
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     // the counters and the outputs start at zero on every call
     DSD_CU(cudaMemsetAsync(scratch, 0, 2 * sizeof(uint32_t), s));
     DSD_CU(cudaMemsetAsync(deg, 0, (size_t)n * sizeof(uint64_t), s));

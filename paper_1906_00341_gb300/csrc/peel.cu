@@ -59,6 +59,9 @@ enum : uint32_t { kErrTimeout = 1, kErrBigOverflow = 2 };
 constexpr uint32_t kSmallFront = 1024;
 constexpr uint32_t kBitmapSlots = 16;   // frontier vertices with a shared bitmap
 constexpr int kChunks = 4;              // 32-entry chunks of a row in flight per warp
+constexpr uint32_t kWarpCand = 32;      // candidate sets a warp handles itself (h >= 4)
+constexpr uint32_t kWarpWords = 3 * kWarpCand;   // a warp's candidates, counters, rows
+constexpr uint32_t kHeavyBit = 4;       // state word: frontier vertex on the heavy list
 
 __device__ __forceinline__ uint32_t st_of(uint32_t w) { return w & 3u; }
 
@@ -68,7 +71,9 @@ struct PeelCtrl {
     uint32_t fcnt[3];
     uint32_t big_cnt[3];
     unsigned long long destroyed[3];
-    uint32_t pad0[16];
+    uint32_t hcnt[3];               // heavy frontier vertices of the round
+    uint32_t grab[3];               // light frontier vertices taken by blocks
+    uint32_t pad0[10];
     uint32_t bar_count;
     uint32_t pad1[31];
     uint32_t bar_gen;
@@ -125,6 +130,8 @@ struct PeelParams {
     ulonglong2* jblk;      // small regime: per-block (slice minimum, alive<<32 | candidates)
     uint2* big;
     uint64_t big_cap;
+    uint32_t* heavy;       // large regime: frontier vertices with long rows
+    uint32_t heavy_min;    // rows longer than this are heavy (0 = no heavy list)
     uint64_t* lvl_k;
     uint32_t* lvl_size;
     uint64_t* lvl_mu;
@@ -132,7 +139,7 @@ struct PeelParams {
     uint64_t wait_ns;
     unsigned long long mu0;
     unsigned long long k0; // initial level: kstart - 1, or 0
-    uint32_t cap;          // per-warp candidate buffer entries (>= max |N+|, >= 32)
+    uint32_t cap;          // candidate buffer of a big item (>= max |N+|, >= 32)
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
     uint32_t asmall;       // small-regime list capacity (0 = regime off)
@@ -273,14 +280,43 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
     __syncthreads();
 }
 
-// Candidates of frontier vertex v among N+(w), in order, into C (one warp).
-// A candidate is alive, or a frontier vertex with a larger id than v, and is
+// Candidates of frontier vertex v among N+(w), in order (one warp).  A
+// candidate is alive, or a frontier vertex with a larger id than v, and is
 // adjacent to v: tested on v's shared bitmap `bm` (over local ids) when
 // given, else by binary search in v's row.  kChunks chunks of the row are
-// loaded at once.
+// loaded at once.  MODE:
+//   kGatherDirect (h = 3): each candidate closes the triangle {v, w, x}; an
+//     alive candidate loses it on the spot; nothing is stored;
+//   kGatherWarp: the first kWarpCand candidates go to C; the walk stops as
+//     soon as there are more (the item then needs a block);
+//   kGatherAll: every candidate goes to C (capacity P.cap).
+// Returns the number of candidates seen.
+enum { kGatherDirect = 0, kGatherWarp = 1, kGatherAll = 2 };
+
+template <int MODE>
+__device__ __forceinline__ void take_candidate(const PeelParams& P, bool ok, bool alive,
+                                               uint32_t x, uint32_t* C, uint32_t& nc,
+                                               unsigned long long k, uint32_t* next,
+                                               uint32_t* next_cnt, unsigned long long& bytes) {
+    unsigned lane = lane_id();
+    unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (MODE == kGatherDirect) {
+        if (ok && alive) {
+            dec_and_queue(P, x, 1ull, k, next, next_cnt);
+            bytes += 16;
+        }
+    } else {
+        uint32_t at = nc + __popc(bal & ((1u << lane) - 1u));
+        if (ok && (MODE == kGatherAll || at < kWarpCand)) C[at] = x;
+    }
+    nc += __popc(bal);
+}
+
+template <int MODE>
 __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint32_t v,
                                                       uint32_t w, uint32_t* C,
-                                                      const uint32_t* bm,
+                                                      const uint32_t* bm, unsigned long long k,
+                                                      uint32_t* next, uint32_t* next_cnt,
                                                       unsigned long long& bytes) {
     unsigned lane = lane_id();
     const uint32_t* Nv = P.wadj + P.off[v];
@@ -313,19 +349,18 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
                 uint64_t p = p0 + u * 32 + lane;
                 bool ok = false;
                 uint32_t x = xs[u];
+                uint32_t s = st_of(ws[u]);
                 if (p < dv) {
                     bytes += 8;
-                    uint32_t s = st_of(ws[u]);
                     if (s == kAlive || (s == kFront && x > v)) {
                         uint64_t pos = lower_bound_u32(Nw, dw, x);
                         ok = pos < dw && Nw[pos] == x;
                         bytes += 4ull * pw;
                     }
                 }
-                unsigned bal = __ballot_sync(0xffffffffu, ok);
-                if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
-                nc += __popc(bal);
+                take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
             }
+            if (MODE == kGatherWarp && nc > kWarpCand) return nc;
         }
         return nc;
     }
@@ -346,9 +381,9 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
             uint64_t p = p0 + u * 32 + lane;
             bool ok = false;
             uint32_t x = xs[u];
+            uint32_t s = st_of(ws[u]);
             if (p < e) {
                 bytes += 8;
-                uint32_t s = st_of(ws[u]);
                 if (s == kAlive || (s == kFront && x > v)) {
                     if (bm) {
                         uint32_t l = ws[u] >> 2;
@@ -360,17 +395,18 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
                     }
                 }
             }
-            unsigned bal = __ballot_sync(0xffffffffu, ok);
-            if (ok) C[nc + __popc(bal & ((1u << lane) - 1u))] = x;
-            nc += __popc(bal);
+            take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
         }
+        if (MODE == kGatherWarp && nc > kWarpCand) return nc;
     }
     return nc;
 }
 
 // One (v, w) work item of a frontier vertex v with h >= 3: the cliques
 // {v, w, ...} whose members other than v are candidates of v and whose
-// smallest such member is w.  Executed by one warp.
+// smallest such member is w.  Executed by one warp; C, cnt, rows are the
+// warp's kWarpCand-entry buffers.  Candidate sets above kWarpCand (h >= 4)
+// are queued as big items for a block.
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
                            uint32_t* rows, uint32_t* big_cnt, const uint32_t* bm,
@@ -380,23 +416,15 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
     if (lane == 0) bytes += 4 + 4;   // w, its state word
     if (!(sw == kAlive || (sw == kFront && w > v))) return;
     if (lane == 0) bytes += 16;      // wnb[w], wend[w]
-    uint32_t nc = gather_candidates(P, v, w, C, bm, bytes);
-    __syncwarp();
     const int r = P.h - 2;
     unsigned long long tot = 0;
     if (r == 1) {
-        tot = nc;
-        for (uint32_t i = lane; i < nc; i += 32) {
-            uint32_t x = C[i];
-            bytes += 4;
-            if (st_of(P.sl[x]) == kAlive) {
-                dec_and_queue(P, x, 1ull, k, next, next_cnt);
-                bytes += 16;
-            }
-        }
+        tot = gather_candidates<kGatherDirect>(P, v, w, C, bm, k, next, next_cnt, bytes);
     } else {
+        uint32_t nc = gather_candidates<kGatherWarp>(P, v, w, C, bm, k, next, next_cnt, bytes);
+        __syncwarp();
         if (nc < (uint32_t)r) return;
-        if (nc > 32 && (r >= 3 || P.big_cap)) {
+        if (nc > kWarpCand) {
             if (lane == 0) {
                 uint32_t at = atomicAdd(big_cnt, 1u);
                 if (at < P.big_cap) P.big[at] = make_uint2(v, w);
@@ -462,12 +490,14 @@ __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigne
     uint32_t* C = smem + 2 * P.cap;                                           // cap
     uint32_t* rows = C + P.cap;                                               // cap * W
     __shared__ uint32_t s_nc;
+    __shared__ uint32_t s_next;
     __shared__ unsigned long long s_tot;
     uint32_t sw = st_of(P.sl[w]);
     if (warp_id() == 0) {
-        uint32_t nc = gather_candidates(P, v, w, C, nullptr, bytes);
+        uint32_t nc = gather_candidates<kGatherAll>(P, v, w, C, nullptr, k, next, next_cnt, bytes);
         if (lane_id() == 0) {
             s_nc = nc;
+            s_next = 0;
             s_tot = 0;
             bytes += 4 + 4 + 16;
         }
@@ -483,7 +513,7 @@ __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigne
     __syncthreads();
     block_build_rows(C, nc, W, P.wend, P.wadj, P.wnb, rows);
     __syncthreads();
-    unsigned long long mine = block_dfs(rows, nc, W, P.h - 2, cnt);
+    unsigned long long mine = block_dfs(rows, nc, W, P.h - 2, cnt, &s_next);
     if (mine) atomicAdd(&s_tot, mine);
     __syncthreads();
     unsigned long long tot = s_tot;
@@ -542,6 +572,7 @@ __device__ __forceinline__ void process_frontier(
     const PeelParams& P, const uint32_t* F, uint32_t nf, unsigned long long k, uint32_t* Fnext,
     uint32_t* next_cnt, uint32_t* big_cnt, uint32_t* wC, unsigned* wCnt, uint32_t* wRows,
     const uint32_t* bm, uint32_t bm_words, unsigned long long* s_pre, unsigned long long* s_red,
+    const uint32_t* hl, uint32_t nh, uint32_t* grab, uint32_t* s_grab,
     unsigned long long& destroyed, unsigned long long& items, unsigned long long& bytes) {
     constexpr int NW = NT / 32;
     const unsigned lane = lane_id(), wid = warp_id();
@@ -612,6 +643,58 @@ __device__ __forceinline__ void process_frontier(
             }
         }
     } else {
+        // Large regime: the items of heavy vertices (hl, nh: rows longer than
+        // heavy_min, flagged kHeavyBit) are flattened over every warp of the
+        // grid in batches of kSmallFront vertices; every other vertex goes to
+        // one block, blocks taking chunks of the frontier from *grab.  In the
+        // small regime (hl null) blocks take the vertices in a fixed order.
+        if (hl) {
+            for (uint32_t b0 = 0; b0 < nh; b0 += kSmallFront) {
+                const uint32_t nb = nh - b0 < kSmallFront ? nh - b0 : kSmallFront;
+                const uint32_t* H = hl + b0;
+                block_prefix_degrees<NT>(P, H, nb, s_pre, s_red);
+                unsigned long long T = s_pre[nb];
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    items += T;
+                    bytes += 20ull * nb;
+                }
+                for (uint64_t t = gwarp; t < T; t += gwarps) {
+                    uint32_t lo = 0, hi = nb;
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (s_pre[mid] <= t) lo = mid; else hi = mid;
+                    }
+                    uint32_t v = H[lo];
+                    uint32_t w = P.wadj[P.off[v] + (t - s_pre[lo])];
+                    process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, nullptr,
+                               destroyed, bytes);
+                }
+                __syncthreads();   // s_pre is rewritten by the next batch
+            }
+            const uint32_t ch0 = nf / (4u * gridDim.x);
+            const uint32_t ch = ch0 < 1u ? 1u : (ch0 > 32u ? 32u : ch0);
+            for (;;) {
+                if (threadIdx.x == 0) *s_grab = atomicAdd(grab, ch);
+                __syncthreads();
+                const uint32_t i0 = *s_grab;
+                __syncthreads();
+                if (i0 >= nf) break;
+                const uint32_t i1 = i0 + ch < nf ? i0 + ch : nf;
+                for (uint32_t i = i0; i < i1; i++) {
+                    uint32_t v = F[i];
+                    if (P.sl[v] & kHeavyBit) continue;   // taken above
+                    uint64_t b = P.off[v], e = P.wend[v];
+                    for (uint64_t p = b + wid; p < e; p += NW)
+                        process_vw(P, v, P.wadj[p], k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt,
+                                   nullptr, destroyed, bytes);
+                    if (threadIdx.x == 0) {
+                        items += e - b;
+                        bytes += 24;
+                    }
+                }
+            }
+            return;
+        }
         for (uint64_t i = blockIdx.x; i < nf; i += gridDim.x) {
             uint32_t v = F[i];
             uint64_t b = P.off[v], e = P.wend[v];
@@ -662,15 +745,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
     __shared__ unsigned long long s_red[NW];
     __shared__ uint32_t s_wtot[NW];
     __shared__ uint32_t s_n;
+    __shared__ uint32_t s_grab;
     PeelCtrl* c = P.ctrl;
     const unsigned lane = lane_id(), wid = warp_id();
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gwarp = gtid >> 5;
     const uint64_t gwarps = gthreads >> 5;
-    uint32_t* wC = smem + (size_t)wid * (2 * P.cap + 32);
-    unsigned* wCnt = wC + P.cap;
-    uint32_t* wRows = wC + 2 * P.cap;
+    uint32_t* wC = smem + (size_t)wid * kWarpWords;
+    unsigned* wCnt = wC + kWarpCand;
+    uint32_t* wRows = wC + 2 * kWarpCand;
     uint32_t* sA = smem + P.work_words;   // small regime: alive list
     uint32_t* sF = sA + P.asmall;         // small regime: frontier
     uint32_t* sBM = sF + P.asmall;        // small regime: neighbourhood bitmaps
@@ -728,9 +812,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             }
             uint32_t fcur = c->fcnt[r % 3];
             uint32_t* Fcur = P.front[r % 3];
-            for (uint64_t i = gtid; i < fcur; i += gthreads) {
-                P.sl[Fcur[i]] = kFront;
-                bytes += 4 + 4;
+            // mark F_r; rows longer than heavy_min also go to the heavy list
+            for (uint64_t base = gwarp * 32; base < fcur; base += gwarps * 32) {
+                uint64_t i = base + lane;
+                bool hv = false;
+                uint32_t v = 0;
+                if (i < fcur) {
+                    v = Fcur[i];
+                    hv = P.heavy_min && P.wend[v] - P.off[v] > P.heavy_min;
+                    P.sl[v] = kFront | (hv ? kHeavyBit : 0u);
+                    bytes += 4 + 4 + (P.heavy_min ? 16 : 0);
+                }
+                if (P.heavy_min) warp_append(hv, v, &c->hcnt[r % 3], P.heavy);
             }
             if (lead) {
                 if (r) {
@@ -739,6 +832,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     c->big_cnt[(r + 2) % 3] = 0;
                 }
                 c->fcnt[(r + 1) % 3] = 0;
+                c->hcnt[(r + 1) % 3] = 0;
+                c->grab[(r + 1) % 3] = 0;
             }
             BARRIER(0);
 
@@ -814,18 +909,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     }
                     for (uint64_t base = gwarp * 32; base < na; base += gwarps * 32) {
                         uint64_t i = base + lane;
-                        bool in = false;
+                        bool in = false, hv = false;
                         uint32_t v = 0;
                         if (i < na) {
                             v = Aout[i];
                             bytes += 4 + 8;
                             if (P.deg[v] <= k) {
                                 in = true;
-                                P.sl[v] = kFront;
-                                bytes += 4 + 4;
+                                hv = P.heavy_min && P.wend[v] - P.off[v] > P.heavy_min;
+                                P.sl[v] = kFront | (hv ? kHeavyBit : 0u);
+                                bytes += 4 + 4 + (P.heavy_min ? 16 : 0);
                             }
                         }
                         warp_append(in, v, &c->fcnt[r % 3], Fcur);
+                        if (P.heavy_min) warp_append(hv, v, &c->hcnt[r % 3], P.heavy);
                     }
                     BARRIER(2);
                     fcur = c->fcnt[r % 3];
@@ -836,7 +933,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 unsigned long long destroyed = 0;
                 process_frontier<NT>(P, Fcur, fcur, k, P.front[(r + 1) % 3],
                                      &c->fcnt[(r + 1) % 3], &c->big_cnt[r % 3], wC, wCnt,
-                                     wRows, nullptr, 0, s_pre, s_red, destroyed, items, bytes);
+                                     wRows, nullptr, 0, s_pre, s_red,
+                                     P.heavy_min ? P.heavy : nullptr, c->hcnt[r % 3],
+                                     &c->grab[r % 3], &s_grab, destroyed, items, bytes);
                 unsigned long long bd = block_sum<NT>(destroyed, s_red);
                 if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
                 BARRIER(3);
@@ -1050,7 +1149,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             unsigned long long destroyed = 0;
             process_frontier<NT>(P, sF, nf_s, k, P.front[(r + 1) % 3], &c->fcnt[(r + 1) % 3],
                                  &c->big_cnt[r % 3], wC, wCnt, wRows, P.h >= 3 ? sBM : nullptr,
-                                 bm_words, s_pre, s_red, destroyed, items, bytes);
+                                 bm_words, s_pre, s_red, nullptr, 0, nullptr, nullptr, destroyed,
+                                 items, bytes);
             unsigned long long bd = block_sum<NT>(destroyed, s_red);
             if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
             BARRIER(7);
@@ -1251,24 +1351,23 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.k0 = kstart ? kstart - 1 : 0;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
     P.compact = h >= 3 ? 1 : 0;
-    if (h >= 5 && maxdplus > kBitmapMax) {
+    if (h >= 4 && maxdplus > kBitmapMax) {
         set_error("h=%d peeling needs at most %u higher-ranked neighbours per vertex "
                   "(max here %u)", h, kBitmapMax, maxdplus);
         return DSD_ERR_UNSUPPORTED;
     }
-    // Big items (candidate sets above 32 vertices, one block each) for
-    // h >= 5, and for h = 4 when every candidate set fits 32-word rows.
-    const bool big_items = h >= 5 || (h == 4 && maxdplus <= kBitmapMax);
+    // Big items (candidate sets above kWarpCand vertices, one block each)
+    // for h >= 4; every candidate set fits 32-word rows.
+    const bool big_items = h >= 4;
     // Shared memory: per-warp candidate buffers (h >= 3) or the big-item
     // bitmap, then the small-regime alive list, frontier and
-    // neighbourhood bitmaps.  Block size: the largest whose candidate
-    // buffers leave room for the small-regime lists.
+    // neighbourhood bitmaps.
     const size_t budget = 220 * 1024;
-    const size_t warp_words = (size_t)2 * P.cap + 32;
-    int NT = 1024;
-    if (h >= 3)
-        while (NT > 256 && (size_t)(NT / 32) * warp_words * 4 > budget / 2) NT >>= 1;
-    size_t work = h >= 3 ? (size_t)(NT / 32) * warp_words : 0;
+    constexpr int NT = 1024;
+    size_t work = h >= 3 ? (size_t)(NT / 32) * kWarpWords : 0;
+    // large-regime frontier vertices with more items than a block's warps
+    // take in four passes have their items spread over the whole grid
+    P.heavy_min = h >= 3 ? 4u * (NT / 32) : 0u;
     if (big_items) {
         size_t W = (P.cap + 31) / 32;
         size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
@@ -1307,6 +1406,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     PeelCtrl* ctrl = nullptr;
     uint32_t* rows_g = nullptr;
     uint2* big = nullptr;
+    uint32_t* heavy = nullptr;
     ulonglong2* jblk = nullptr;
     dsd_status st = DSD_OK;
     PeelCtrl hc;
@@ -1326,6 +1426,8 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
         P.big_cap = g->m * 2 + 1;
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
     }
+    if (P.heavy_min && (st = dalloc(&heavy, n, s)) != DSD_OK) goto done;
+    P.heavy = heavy;
     P.sl = sl;
     P.alive[0] = lists;
     P.alive[1] = lists + n;
@@ -1347,11 +1449,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
         note_launch();
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
-        if (NT == 1024) e = launch_peel<1024>(P, sms, smem, s, &grid);
-        else if (NT == 512) e = launch_peel<512>(P, sms, smem, s, &grid);
-        else e = launch_peel<256>(P, sms, smem, s, &grid);
-    }
+    if (e == cudaSuccess) e = launch_peel<NT>(P, sms, smem, s, &grid);
     if (e == cudaSuccess && P.tail_max) {
         // the launches run only if something was handed over (they read tail_n)
         TailParams T;
@@ -1428,6 +1526,7 @@ done:
     dev_free(ctrl, s);
     dev_free(rows_g, s);
     dev_free(big, s);
+    dev_free(heavy, s);
     dev_free(jblk, s);
     return st;
 }

@@ -355,10 +355,13 @@ using namespace dsd;
 
 extern "C" {
 
-dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* M, uint32_t* kmax_core,
-                               uint32_t* densest, int mem, dsd_core_app_result* r,
-                               dsd_seed_info* info) {
+dsd_status dsd_core_app_seeded_info(dsd_graph* g, int h, const dsd_model* Mc,
+                                    uint32_t* kmax_core, uint32_t* densest, int mem,
+                                    dsd_core_app_result* r, dsd_seed_info* info) {
     set_error("");
+    // the proposal reads the weights; the model's device work buffers are
+    // scratch that the call may overwrite
+    dsd_model* M = const_cast<dsd_model*>(Mc);
     if (!g || !M || !r || h < 2 || h > DSD_MAX_H || (mem != DSD_MEM_HOST && mem != DSD_MEM_DEVICE)) {
         set_error("invalid argument to dsd_core_app_seeded");
         return DSD_ERR_INVALID;
@@ -433,14 +436,22 @@ dsd_status dsd_core_app_seeded(dsd_graph* g, int h, dsd_model* M, uint32_t* kmax
             r->densest_size = hs.densest_size;
             r->densest_mu = hs.densest_mu;
             r->nlevels = hs.nlevels;
+            r->seeded_accepted = 1;
+            r->seed_k = k;
             if (info) *info = si;
             return DSD_OK;
         }
     }
     // ---- rejected (or no usable proposal): the plain path
     st = dsd_core_app(g, h, kmax_core, densest, mem, r);
+    if (st == DSD_OK) r->seed_k = si.seed_k;
     if (info) *info = si;
     return st;
+}
+
+dsd_status dsd_core_app_seeded(dsd_graph* g, int h, const dsd_model* m, uint32_t* kmax_core,
+                               uint32_t* densest, int mem, dsd_core_app_result* r) {
+    return dsd_core_app_seeded_info(g, h, m, kmax_core, densest, mem, r, nullptr);
 }
 
 }  // extern "C"

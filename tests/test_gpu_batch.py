@@ -99,3 +99,37 @@ def test_batch_autotune_cache(L, tmp_path):
     r2 = b2.results()
     assert r1 == r2
     b2.close()
+
+
+def test_batch_run_over_handles(L, orc):
+    """dsd_batch_run on existing graph handles: graphs within the batch
+    kernel's limits run in one launch, the others (n > 65535, h > 4) through
+    the single-graph path inside the same call; every result and core array
+    equals dsd_core_app / dsd_core_decompose on that handle, and a sample
+    equals the oracle."""
+    graphs = gg.batch(20, nmax=3000, nmedian=400.0)
+    big = gg.chung_lu(70000, 200000, 2.3, 300.0, 5)
+    graphs.append((big[0], big[1], big[2], 3))          # beyond the batch kernel's n
+    n5, s5, d5 = gg.random_small(60, 0.5, seed=9)
+    graphs.append((n5, s5, d5, 5))                      # beyond its h
+    handles = [L.Graph.from_edges(n, s, d) for n, s, d, _ in graphs]
+    try:
+        hs = [h for _, _, _, h in graphs]
+        res = L.dsd_batch_run(handles, hs, want_cores=True)
+        for i, ((n, s, d, h), g, r) in enumerate(zip(graphs, handles, res)):
+            want = g.core_app(h, sets=False)
+            core, kmax = g.core_decompose(h)
+            for key in ("kmax", "kmax_core_size", "kmax_core_mu", "best_k", "densest_size",
+                        "densest_mu", "nlevels"):
+                assert r[key] == want[key], (i, key)
+            assert np.array_equal(r["core"], core), i
+            if i % 5 == 0 or i >= len(graphs) - 2:
+                ocore, ok = orc.core_decompose(orc.csr(n, s, d), h)
+                assert np.array_equal(r["core"], ocore) and r["kmax"] == ok, i
+        # no core arrays wanted, empty call
+        res2 = L.dsd_batch_run(handles[:3], hs[:3])
+        assert [x["kmax"] for x in res2] == [x["kmax"] for x in res[:3]]
+        assert L.dsd_batch_run([], []) == []
+    finally:
+        for g in handles:
+            g.close()

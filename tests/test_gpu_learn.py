@@ -268,6 +268,8 @@ def _check_seeded(L, orc, n, s, d, h, targets):
             info = r["seed"]
             acc, kx = _expected_accept(orc, og, h, info["rho_prime"], core2)
             assert info["accepted"] == int(acc), (t, info)
+            # the result record carries the same decision
+            assert r["seeded_accepted"] == info["accepted"] and r["seed_k"] == info["seed_k"]
             seen.add(bool(acc))
             if kx is not None:
                 assert info["seed_k"] == kx[0]
@@ -288,6 +290,12 @@ def _check_seeded(L, orc, n, s, d, h, targets):
             # the plain call on the same graph still agrees afterwards
             p = g.core_app(h)
             assert p["kmax"] == w["kmax"] and p["best_k"] == w["best_k"]
+            # the boundary's seven-argument call answers the same
+            rr = L.dsd_core_app_seeded(g.handle, h, M.handle, 0, 0, L.DSD_MEM_HOST)
+            assert (int(rr.kmax), int(rr.best_k), int(rr.densest_mu), int(rr.densest_size),
+                    int(rr.seeded_accepted), int(rr.seed_k)) == (
+                w["kmax"], w["best_k"], w["densest_mu"], w["densest_size"], info["accepted"],
+                info["seed_k"])
     return seen
 
 

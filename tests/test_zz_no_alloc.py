@@ -51,6 +51,21 @@ def test_noalloc_matches_clique_degrees(L, graph):
             assert np.array_equal(got, want_deg), ("deg", call)
 
 
+def test_noalloc_edgeless_graph(L):
+    """Vertices but no edges: a null adj is accepted and every count is 0."""
+    import torch
+    n = 1000
+    off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        deg = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+        mu = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        L.dsd_triangle_degrees_noalloc(n, off.data_ptr(), 0, deg.data_ptr(), mu.data_ptr(),
+                                       stream)
+        torch.cuda.synchronize()
+        assert int(mu.item()) == 0 and int(deg.abs().sum().item()) == 0, call
+
+
 def test_noalloc_rejects_too_many_vertices(L):
     with pytest.raises(L.DSDError) as ei:
         L.dsd_triangle_degrees_noalloc(1 << 21, 1, 1, 1, 1, 0)
