@@ -22,7 +22,12 @@ more objects on the same line (rank 0, skipped with --no-learned /
              persistent batch kernel vs a host loop of the plain path;
   exact   -- CoreExact (dsd_core_exact) on the step's graph with its
              decomposition cached: device time of the exact stage, rho_opt
-             against the densest level's density, the flow network's size.
+             against the densest level's density, the flow network's size;
+  c3      -- R-MAT scale 22 (4,194,304 vertices, 16 x 2^22 draws, (0.57,
+             0.19, 0.19, 0.05)), h = 4 and h = 5: the same dsd_core_app call
+             (device edge list -> CoreApp outputs), its listing and (k,Psi)-
+             peel phases, h-cliques/s, and the listing's roofline under both
+             byte models (skipped with --no-c3; --c3-h lists the h values).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -65,8 +70,17 @@ def parse(argv=None):
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched leg (4096 mixed graphs)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--heldout", type=int, default=20,
+                    help="held-out graphs (n 200k..4M) the trained proposal is evaluated on")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the CoreExact leg")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the R-MAT scale 22 leg (h = 4 and 5)")
+    ap.add_argument("--c3-h", default="4,5",
+                    help="clique sizes of the R-MAT scale 22 leg (comma separated)")
+    ap.add_argument("--c3-steps", type=int, default=1,
+                    help="timed calls per h of the R-MAT scale 22 leg (after one warm-up "
+                         "call at h = 4)")
     ap.add_argument("--exact-only", action="store_true",
                     help="run only the CoreExact leg and print it (a short command for "
                          "kernel profiles)")
@@ -201,6 +215,8 @@ def run_ours(args, rank, world, local):
     deg_mu = np.zeros(1, np.uint64)
     L.dsd_clique_degrees(hnd, h, 0, deg_mu.ctypes.data, L.DSD_MEM_HOST)
     mu = int(deg_mu[0])
+    pk, pk_kind = peaks()
+    roof_listing = listing_roofline(L, hnd, float(ms[3]), pk, pk_kind, "count")
     L.dsd_graph_destroy(hnd)
 
     for _ in range(args.warmup):
@@ -294,6 +310,7 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": 8 * m_draws, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "roofline_listing": roof_listing,
         "clocks": clocks,
         "peel_stats": pstats,
     }
@@ -379,7 +396,9 @@ def run_learned(args, local):
                        sub_m=int(info.sub_m))
         out[name] = rec
     torch.cuda.synchronize()
+    heldout = run_heldout(args, local, M) if args.heldout > 0 else None
     return {
+        "heldout": heldout,
         "workload": "chung_lu n=4e6 draws=6.4e7 beta=2.2 wmax=sqrt(1.28e8) + 5 x G(300,0.4), h=3",
         "checkpoint": M.header.get("sha256", "")[:16],
         "train_graphs": M.header.get("meta", {}).get("graphs"),
@@ -393,6 +412,80 @@ def run_learned(args, local):
         "topdown": out["topdown"],
         "timing": "CUDA events per call (CSR build + decomposition), mean of %d after %d "
                   "warm-up, L2 flushed between calls" % (args.steps, args.warmup),
+    }
+
+
+def _heldout_graph(i):
+    from paper_1906_00341_gb300 import graphgen as gg
+    return gg.heldout_graph(i)
+
+
+def run_heldout(args, local, M):
+    """The trained proposal on --heldout graphs it never saw (Chung-Lu with
+    planted blocks, n 200k..4M, h = 3): per graph one plain and one seeded
+    call (CSR build included in both, CUDA events), outputs compared; the
+    acceptance rate and the speedups, fallbacks included."""
+    import multiprocessing as mp
+    import torch
+    from paper_1906_00341_gb300 import _lib as L
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    per = []
+    t_plain = t_seed = 0.0
+    with mp.get_context("spawn").Pool(8) as pool:
+        for i, (n, s, d, h) in enumerate(pool.imap(_heldout_graph, range(args.heldout))):
+            src = torch.from_numpy(s.astype(np.int32)).to(dev)
+            dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+            kc = torch.empty(n, dtype=torch.int32, device=dev)
+            de = torch.empty(n, dtype=torch.int32, device=dev)
+            res = {}
+            for name in ("warm", "plain", "seeded"):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(),
+                                           L.DSD_MEM_DEVICE, sp)
+                if name == "seeded":
+                    r, info = L.dsd_core_app_seeded_info(g, h, M.handle, kc.data_ptr(),
+                                                         de.data_ptr(), L.DSD_MEM_DEVICE)
+                else:
+                    r = L.dsd_core_app(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
+                    info = None
+                e1.record(stream)
+                e1.synchronize()
+                res[name] = (e0.elapsed_time(e1), r, info,
+                             kc[: r.kmax_core_size].cpu().numpy().tobytes(),
+                             de[: r.densest_size].cpu().numpy().tobytes())
+                L.dsd_graph_destroy(g)
+            tp, rp, _, kp, dp = res["plain"]
+            ts, rs, info, ks, ds = res["seeded"]
+            same = ((int(rp.kmax), int(rp.best_k), int(rp.densest_mu), int(rp.densest_size),
+                     kp, dp) == (int(rs.kmax), int(rs.best_k), int(rs.densest_mu),
+                                 int(rs.densest_size), ks, ds))
+            t_plain += tp
+            t_seed += ts
+            per.append({"n": n, "draws": int(s.size), "plain_ms": round(tp, 2),
+                        "seeded_ms": round(ts, 2), "speedup": round(tp / ts, 3),
+                        "accepted": int(info.accepted), "rho_prime": float(info.rho_prime),
+                        "rho_densest": int(rp.densest_mu) / max(int(rp.densest_size), 1),
+                        "sub_n": int(info.sub_n), "identical": bool(same)})
+            del src, dst, kc, de
+    acc = [p["accepted"] for p in per]
+    sp_ = [p["speedup"] for p in per]
+    return {
+        "graphs": len(per),
+        "recipe": "graphgen.heldout_graph(i), i = 0..%d: Chung-Lu n log-uniform in [2e5, 4e6], "
+                  "16 n draws, exponent U[2.1, 2.4], 1-5 planted G(150..300, 0.3..0.5); "
+                  "seeds disjoint from training" % (len(per) - 1),
+        "acceptance_rate": float(np.mean(acc)) if acc else None,
+        "identical_all": all(p["identical"] for p in per),
+        "speedup_total": t_plain / t_seed if t_seed else None,
+        "speedup_geomean": float(np.exp(np.mean(np.log(sp_)))) if sp_ else None,
+        "speedup_min": min(sp_) if sp_ else None, "speedup_max": max(sp_) if sp_ else None,
+        "per_graph": per,
+        "timing": "CUDA events per call (CSR build + CoreApp), one call each after one "
+                  "warm-up plain call",
     }
 
 
@@ -420,7 +513,7 @@ def run_batched(args, local, graphs):
     sp = stream.cuda_stream
     cache = os.path.join(OUT_DIR, "batch_autotune.txt")
     B = L.Batch(graphs, want_cores=False, stream=stream, autotune_cache=cache)
-    threads, cps, tuned = B.info()
+    threads, cps, lpr, tuned = B.info()
     for _ in range(args.warmup):
         B.run()
     torch.cuda.synchronize()
@@ -476,7 +569,10 @@ def run_batched(args, local, graphs):
         "loop_graphs_per_s": len(graphs) / (loop_ms / 1e3), "loop_ms": loop_ms,
         "speedup": loop_ms / batch_ms, "graphs_ok": ok,
         "loop_mismatches": mismatch, "loop_sample": len(sub),
-        "autotuned": {"threads": int(threads), "ctas_per_sm": int(cps), "ms": float(tuned)},
+        "autotuned": {"threads": int(threads), "ctas_per_sm": int(cps),
+                      "lanes_per_row": int(lpr), "ms": float(tuned),
+                      "search": "threads x CTAs/SM {512x1, 256x2, 512x2, 1024x1, 256x1} at "
+                                "32 lanes per row, then lanes per row {16, 8} at the best"},
         "timing": "CUDA events; batch: mean of %d replays after %d; loop: one pass over every "
                   "8th graph after a checked pass, scaled to the batch" % (args.steps, args.warmup),
     }
@@ -484,13 +580,18 @@ def run_batched(args, local, graphs):
 
 # ------------------------------------------------------------- CPU side
 
-def cpu_sample(n, s, d, frac=0.75, seed=99):
-    """Induced subgraph on a seeded random fraction of the vertices."""
-    rng = np.random.default_rng(seed)
-    keep = rng.random(n) < frac
-    newid = np.cumsum(keep) - 1
-    sel = keep[s] & keep[d]
-    return int(keep.sum()), newid[s[sel]].astype(np.uint32), newid[d[sel]].astype(np.uint32)
+def host_cpu():
+    """Host core count and CPU model (for the baseline's record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
 
 
 def time_oracle(n, s, d, h):
@@ -506,25 +607,29 @@ def time_oracle(n, s, d, h):
 
 
 def run_reference(args, rank, world):
+    """The oracle (plain single-threaded C) on the full workload graph, the
+    GPU arm's configuration: CSR build + Algorithm 3 + the CoreApp outputs
+    per step.  One untimed warm-up step at most (an oracle run has nothing
+    to warm beyond the page cache), then --steps timed steps."""
     from paper_1906_00341_gb300 import graphgen as gg
     n, s, d, _ = gg.workload(args.workload)
-    ns, ss, ds = cpu_sample(n, s, d)
     times, mu = [], 0
-    for i in range(args.warmup + args.steps):
-        t, mu, _ = time_oracle(ns, ss, ds, args.h)
-        if i >= args.warmup:
+    for i in range(min(args.warmup, 1) + args.steps):
+        t, mu, _ = time_oracle(n, s, d, args.h)
+        if i >= min(args.warmup, 1):
             times.append(t)
     ms = 1e3 * float(np.mean(times))
     v = mu / (ms / 1e3)
-    sample = "induced subgraph on a seeded 75%% vertex sample (n=%d, %d draws), h=%d" % (
-        ns, ss.size, args.h)
+    sample = ("full workload graph (n=%d, %d draws), h=%d: oracle CSR build + Algorithm 3 + "
+              "CoreApp outputs, single thread, mean of %d runs" % (n, s.size, args.h, len(times)))
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "h-cliques/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": args.workload, "h": args.h, "sample": sample},
+        "data": "synthetic", "config": {"workload": args.workload, "h": args.h, "sample": sample,
+                                         "same_config": True},
         "cpu_baseline": {"value": v, "unit": "h-cliques/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": v, "unit": "h-cliques/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -582,6 +687,107 @@ def run_exact(args, local):
     }
 
 
+# ------------------------------------------------------ R-MAT scale 22
+
+def listing_roofline(L, hnd, count_ms, peak, peak_kind, traffic_key=None):
+    """Achieved bandwidth of the listing phase under the kernels' staging
+    model and under the merge-intersection model, against the HBM peak."""
+    staged, merge = L.dsd_listing_bytes(hnd)
+    out = {"bound": "hbm", "kernel": "count", "ms": count_ms, "peak": peak,
+           "peak_kind": peak_kind, "unit": "GB/s", "bytes_staged": staged,
+           "bytes_merge": merge}
+    if count_ms and count_ms > 0:
+        out["achieved_staged"] = staged / (count_ms / 1e3) / 1e9
+        out["achieved_merge"] = merge / (count_ms / 1e3) / 1e9
+        out["frac_staged"] = out["achieved_staged"] / peak
+        out["frac_merge"] = out["achieved_merge"] / peak
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if traffic_key and os.path.exists(tp):
+        try:
+            out["traffic"] = json.load(open(tp)).get(traffic_key)
+        except Exception:
+            pass
+    return out
+
+
+def run_c3(args, local):
+    """dsd_core_app on R-MAT scale 22 for each h of --c3-h: device time of
+    the whole call (CSR build included) by CUDA events, the listing and peel
+    phases from the library's phase events (a separate instrumented call),
+    h-cliques/s = mu / call time, and the listing roofline."""
+    import torch
+    from paper_1906_00341_gb300 import graphgen as gg
+    from paper_1906_00341_gb300 import _lib as L
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    t0 = time.perf_counter()
+    n, s, d, _ = gg.workload("rmat22")
+    gen_s = time.perf_counter() - t0
+    src = torch.from_numpy(s.astype(np.int32)).to(dev)
+    dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+    kc = torch.empty(n, dtype=torch.int32, device=dev)
+    de = torch.empty(n, dtype=torch.int32, device=dev)
+    peak, peak_kind = peaks()
+    L.dsd_set_wait_limit_ms(600000)
+    out = {"workload": "rmat scale=22 edge_factor=16 (0.57,0.19,0.19,0.05), labels permuted, "
+                       "symmetrised, loops and repeats dropped",
+           "n": n, "draws": int(s.size), "generate_s": gen_s, "runs": {}}
+    hs = [int(x) for x in str(args.c3_h).split(",") if x.strip()]
+
+    def call(h, profile=False):
+        g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE,
+                                   sp)
+        if profile:
+            L.dsd_set_profiling(g, True)
+        r = L.dsd_core_app(g, h, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
+        return g, r
+
+    for h in hs:
+        if h == hs[0]:
+            g, _ = call(h)            # warm-up (module load, pool growth)
+            L.dsd_graph_destroy(g)
+        # instrumented call: phase times, peel statistics, mu, byte models
+        g, r0 = call(h, profile=True)
+        ms, by, la = L.dsd_phase_stats(g)
+        ps = L.dsd_peel_stats(g, 1)
+        mu = np.zeros(1, np.uint64)
+        L.dsd_clique_degrees(g, h, 0, mu.ctypes.data, L.DSD_MEM_HOST)
+        mu = int(mu[0])
+        n_, m_und = L.dsd_graph_info(g)
+        roof = listing_roofline(L, g, float(ms[3]), peak, peak_kind, "count_rmat22")
+        L.dsd_graph_destroy(g)
+        times = []
+        for _ in range(max(args.c3_steps, 1)):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g, r = call(h)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            L.dsd_graph_destroy(g)
+        call_ms = float(np.mean(times))
+        out["m"] = int(m_und)
+        out["runs"][str(h)] = {
+            "h": h, "mu": mu, "call_ms": call_ms, "calls": len(times),
+            "h_cliques_per_s": mu / (call_ms / 1e3),
+            "phase_ms": {nm: round(float(x), 3) for nm, x in zip(L.PHASES, ms)},
+            "kmax": int(r0.kmax), "nlevels": int(r0.nlevels), "best_k": int(r0.best_k),
+            "densest": [int(r0.densest_mu), int(r0.densest_size)],
+            "kmax_core_size": int(r0.kmax_core_size),
+            "peel": {k: ps[k] for k in ("rounds", "levels", "items", "barrier_ns", "barriers",
+                                        "small_round")},
+            "roofline_listing": roof,
+        }
+    L.dsd_set_wait_limit_ms(20000)
+    out["timing"] = ("CUDA events around one dsd_graph_from_edges + dsd_core_app call (device "
+                     "edge list, device outputs); phases from a separate instrumented call; "
+                     "inputs (1 GB CSR) larger than L2")
+    return out
+
+
 def run_once(args, local):
     import torch
     from paper_1906_00341_gb300 import graphgen as gg
@@ -630,13 +836,19 @@ def main():
             line["batched"] = run_batched(args, local, graphs)
         if not args.no_exact:
             line["exact"] = run_exact(args, local)
+        if not args.no_c3:
+            line["c3"] = run_c3(args, local)
         if not args.no_cpu_baseline and world == 1:
-            ns, ss, ds = cpu_sample(n, s, d)
-            t, smu, _ = time_oracle(ns, ss, ds, h)
+            t, smu, _ = time_oracle(n, s, d, h)
             line["cpu_baseline"] = {
                 "value": smu / t, "unit": "h-cliques/s", "cores": 1, "kind": "oracle",
-                "sample": "induced subgraph on a seeded 75%% vertex sample (n=%d, %d draws), "
-                          "h=%d, one run (%.1f s)" % (ns, ss.size, h, t)}
+                "sample": "full C2 graph (n=%d, %d draws), h=%d: one run of the oracle's CSR "
+                          "build + Algorithm 3 + CoreApp outputs (%.1f s; one run, not best of "
+                          "3, to keep the bench within minutes)" % (n, s.size, h, t),
+                "threads_note": "single thread: the oracle is plain sequential C (Algorithm 3's "
+                                "bucket peel removes one vertex at a time); no multi-core "
+                                "variant of it is built",
+                "host": host_cpu()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

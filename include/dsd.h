@@ -286,6 +286,33 @@ dsd_status dsd_core_app_seeded_info(dsd_graph* g, int h, const dsd_model* m,
                                     uint32_t* kmax_core, uint32_t* densest, int mem,
                                     dsd_core_app_result* r, dsd_seed_info* info);
 
+/* ------------------------------------------------------------- PeelApp */
+
+typedef struct {
+    uint64_t mu;              /* h-cliques inside the returned set */
+    uint32_t size;            /* its vertices; its density is mu / size exactly */
+    uint32_t removed;         /* vertices removed when the set was met (n - size) */
+    uint64_t level_k;         /* the (k,Psi)-core level the set was met in */
+} dsd_peel_app_result;
+
+/* PeelApp (Algorithm 2, Sec. 3.2): remove one vertex of minimum current
+ * clique-degree at a time (ties: the smaller vertex id) and return the
+ * densest of the sets met -- G and every residual -- where a later set
+ * replaces the best only when strictly denser.  Its guarantee is Lemma 2
+ * (density >= rho_opt / h).  The removal order passes through every
+ * (k,Psi)-core R_k and removes R_k \ R_{k+1} while in it, so after one
+ * decomposition every level is peeled independently on the GPU.
+ *   densest (capacity n, may be NULL): the returned set, ascending;
+ *   order (capacity n, may be NULL): the removal order, order[i] = the
+ *       vertex removed at step i;
+ *   both host or device memory per mem; res must not be NULL.
+ * With n = 0 all fields are 0.  Errors: DSD_ERR_INVALID; DSD_ERR_UNSUPPORTED
+ * (h >= 4 with more than 1024 higher-ranked neighbours at a vertex);
+ * DSD_ERR_NOMEM; DSD_ERR_TIMEOUT (the decomposition's wait limit);
+ * DSD_ERR_CUDA. */
+dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint32_t* order, int mem,
+                        dsd_peel_app_result* res);
+
 /* ---------------------------------------------- CoreApp's top-down schedule */
 
 typedef struct {
@@ -404,8 +431,9 @@ dsd_status dsd_pattern_core_app(dsd_graph* g, int pattern, int x, uint32_t* kmax
  *   mem: where src/dst live (copied at creation; the caller may free them).
  *   want_cores != 0 keeps every graph's core numbers for dsd_batch_results.
  *   autotune_cache: text file (may be NULL) remembering the launch shape
- *   chosen for a batch signature; without an entry, creation times a few
- *   shapes (threads per CTA, CTAs per SM) on the batch itself.
+ *   chosen for a batch signature; without an entry, creation times shapes on
+ *   the batch itself: threads per CTA x CTAs per SM, then the intersection
+ *   tile (lanes per row scan) at the best of those.
  * Errors: DSD_ERR_INVALID, DSD_ERR_UNSUPPORTED (n, h or m out of range),
  * DSD_ERR_NOMEM, DSD_ERR_CUDA. */
 typedef struct dsd_batch dsd_batch;
@@ -416,13 +444,25 @@ dsd_status dsd_batch_create(uint32_t count, const uint32_t* n, const int* h, con
 dsd_status dsd_batch_replay(dsd_batch* b);
 /* Results of the last run (synchronises the stream).  res: count entries
  * (the fields of dsd_core_app_result; kmax_core/densest sets are not kept);
- * status: count entries, 0 ok, 1 invalid graph, 2 unsupported (h = 4 with
- * more than 512 higher-ranked neighbours); cores: sum of n[i] entries in
- * graph order, or NULL.  Any pointer may be NULL. */
+ * status: count entries, 0 ok, 1 invalid graph (an endpoint >= n); cores:
+ * sum of n[i] entries in graph order, or NULL (needs want_cores).  Any
+ * pointer may be NULL.  Graphs beyond the batch kernel's limits (h = 4 with
+ * more than 512 higher-ranked neighbours at a vertex) are answered by the
+ * single-graph path, from the batch's device edge lists, at the first call
+ * after a run (their results are kept for later calls). */
 dsd_status dsd_batch_results(dsd_batch* b, dsd_core_app_result* res, int* status, uint64_t* cores);
-/* Chosen launch shape and its timed duration (ms, 0 if read from the cache). */
+/* Chosen launch shape -- threads per CTA, CTAs per SM, and the intersection
+ * tile: lanes that scan one row (32, 16 or 8; a warp scans 32 / lanes rows
+ * at once in the triangle listing and the h = 4 edge counts) -- and its
+ * timed duration (ms, 0 if read from the cache or set).  Any pointer may be
+ * NULL. */
 dsd_status dsd_batch_info(const dsd_batch* b, uint32_t* threads, uint32_t* ctas_per_sm,
-                          float* tuned_ms);
+                          uint32_t* lanes_per_row, float* tuned_ms);
+/* Replace the tuned shape (threads 256/512/1024, ctas_per_sm 1 or 2,
+ * lanes_per_row 8/16/32) and capture the launch again; results do not depend
+ * on it.  DSD_ERR_UNSUPPORTED if the shape does not fit on an SM. */
+dsd_status dsd_batch_set_shape(dsd_batch* b, uint32_t threads, uint32_t ctas_per_sm,
+                               uint32_t lanes_per_row);
 void dsd_batch_destroy(dsd_batch* b);
 
 /* CoreApp outputs (no vertex sets) for `count` existing graph handles in one

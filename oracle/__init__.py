@@ -79,7 +79,7 @@ def _load():
                                       ctypes.POINTER(ctypes.c_int)]
     lib.orc_densest_check.restype = ctypes.c_int
     lib.orc_peel_app.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u8p, _u64p,
-                                 _u64p]
+                                 _u64p, _u32p]
     lib.orc_peel_app.restype = ctypes.c_int
     for f in ("orc_pattern_degrees", "orc_pattern_core_decompose", "orc_pattern_level_stats"):
         getattr(lib, f).restype = ctypes.c_int
@@ -256,15 +256,17 @@ def exact_cds(g: Graph, h: int):
 def peel_app(g: Graph, h: int):
     """Algorithm 2 (PeelApp): the densest of G and its residuals under
     one-at-a-time removal of a minimum clique-degree vertex (ties: smaller
-    id).  Returns dict(set = sorted ids, mu, size)."""
+    id).  Returns dict(set = sorted ids, mu, size, order = the removal
+    order)."""
     lib = _load()
     mark = np.zeros(max(g.n, 1), np.uint8)
     mu = np.zeros(1, np.uint64)
     size = np.zeros(1, np.uint64)
+    order = np.zeros(max(g.n, 1), np.uint32)
     _check(lib.orc_peel_app(g.n, _p(g.off, _u64p), _p(g.adj, _u32p), h, _p(mark, _u8p),
-                            _p(mu, _u64p), _p(size, _u64p)))
+                            _p(mu, _u64p), _p(size, _u64p), _p(order, _u32p)))
     return dict(set=np.flatnonzero(mark[:g.n]).astype(np.uint32), mu=int(mu[0]),
-                size=int(size[0]))
+                size=int(size[0]), order=order[:g.n])
 
 
 def densest_check(g: Graph, h: int, p: int, q: int):

@@ -1201,9 +1201,10 @@ static void visit_peel_exact(lister* L, const uint32_t* c) {
  * densest of the sets met.  The sets are G itself and every residual; a
  * later set replaces the best only when strictly denser.  in_best[v]
  * (original ids) marks the best set; *mu_out and *size_out are its clique
- * count and size (with no h-clique: G, 0 cliques). */
+ * count and size (with no h-clique: G, 0 cliques).  order_out (may be NULL,
+ * n entries) receives the removal order in original ids. */
 int orc_peel_app(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
-                 uint8_t* in_best, uint64_t* mu_out, uint64_t* size_out) {
+                 uint8_t* in_best, uint64_t* mu_out, uint64_t* size_out, uint32_t* order_out) {
     if (check_h(h)) return ORC_EINVAL;
     wgraph g;
     if (wg_make(n, off, adj, &g)) return ORC_ENOMEM;
@@ -1243,6 +1244,8 @@ int orc_peel_app(uint32_t n, const uint64_t* off, const uint32_t* adj, int h,
     }
     for (uint32_t i = 0; i < n; i++) in_best[i] = 0;
     for (uint64_t j = bstep; j < n; j++) in_best[g.old_of[order[j]]] = 1;
+    if (order_out)
+        for (uint32_t j = 0; j < n; j++) order_out[j] = g.old_of[order[j]];
     *mu_out = bmu;
     *size_out = bsize;
     rc = ORC_OK;

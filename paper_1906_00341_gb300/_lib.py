@@ -44,6 +44,11 @@ class CoreAppResult(ctypes.Structure):
                 ("seed_k", ctypes.c_uint64)]
 
 
+class PeelAppResult(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_uint64), ("size", ctypes.c_uint32),
+                ("removed", ctypes.c_uint32), ("level_k", ctypes.c_uint64)]
+
+
 class TopdownInfo(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_uint32), ("sub_n", ctypes.c_uint32), ("x", ctypes.c_uint64),
                 ("gamma_out", ctypes.c_uint64), ("sub_m", ctypes.c_uint64)]
@@ -99,11 +104,13 @@ SIGNATURES = {
                                 ctypes.POINTER(_P)]),
     "dsd_batch_replay": (_int, [_P]),
     "dsd_set_checked": (_int, [_int]),
+    "dsd_peel_app": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(PeelAppResult)]),
     "dsd_listing_bytes": (_int, [_P, _P, _P]),
     "dsd_checked_add_selftest": (_int, [_u64, _P, _u32, _P, _P]),
     "dsd_batch_run": (_int, [_int, _P, _P, _P, _P, ctypes.c_char_p]),
     "dsd_batch_results": (_int, [_P, _P, _P, _P]),
-    "dsd_batch_info": (_int, [_P, _P, _P, _P]),
+    "dsd_batch_info": (_int, [_P, _P, _P, _P, _P]),
+    "dsd_batch_set_shape": (_int, [_P, _u32, _u32, _u32]),
     "dsd_batch_destroy": (None, [_P]),
     "dsd_triangle_degrees_noalloc": (_int, [_u32, _P, _P, _P, _P, _P]),
     "dsd_set_profiling": (_int, [_P, _int]),
@@ -190,6 +197,12 @@ def dsd_listing_bytes(g):
     b = _u64()
     _check(load().dsd_listing_bytes(g, ctypes.addressof(a), ctypes.addressof(b)))
     return int(a.value), int(b.value)
+
+
+def dsd_peel_app(g, h, densest_ptr, order_ptr, mem):
+    r = PeelAppResult()
+    _check(load().dsd_peel_app(g, h, densest_ptr, order_ptr, mem, ctypes.byref(r)))
+    return r
 
 
 def dsd_set_checked(on):
@@ -316,9 +329,15 @@ def dsd_batch_results(b, res_ptr, status_ptr, cores_ptr):
 def dsd_batch_info(b):
     t = _u32()
     c = _u32()
+    lp = _u32()
     ms = ctypes.c_float()
-    _check(load().dsd_batch_info(b, ctypes.addressof(t), ctypes.addressof(c), ctypes.addressof(ms)))
-    return int(t.value), int(c.value), float(ms.value)
+    _check(load().dsd_batch_info(b, ctypes.addressof(t), ctypes.addressof(c),
+                                 ctypes.addressof(lp), ctypes.addressof(ms)))
+    return t.value, c.value, lp.value, ms.value
+
+
+def dsd_batch_set_shape(b, threads, ctas_per_sm, lanes_per_row):
+    _check(load().dsd_batch_set_shape(b, threads, ctas_per_sm, lanes_per_row))
 
 
 def dsd_batch_destroy(b):
@@ -369,7 +388,11 @@ class Batch:
         return out
 
     def info(self):
+        """(threads, ctas_per_sm, lanes_per_row, tuned_ms)"""
         return dsd_batch_info(self.handle)
+
+    def set_shape(self, threads, ctas_per_sm, lanes_per_row):
+        dsd_batch_set_shape(self.handle, threads, ctas_per_sm, lanes_per_row)
 
     def close(self):
         if self.handle:
@@ -685,6 +708,14 @@ class Graph:
                         DSD_MEM_HOST)
         c = int(nl[0])
         return k[:c], s[:c], mu[:c]
+
+    def peel_app(self, h, mem="host"):
+        """PeelApp (Algorithm 2): the set, its mu and size, the removal order."""
+        de = self._alloc(self.n, 4, mem)
+        od = self._alloc(self.n, 4, mem)
+        r = dsd_peel_app(self.handle, h, self._ptr(de), self._ptr(od), self._memc(mem))
+        return dict(set=de[: r.size], mu=int(r.mu), size=int(r.size), removed=int(r.removed),
+                    level_k=int(r.level_k), order=od[: self.n])
 
     def core_app(self, h, mem="host", sets=True):
         kc = self._alloc(self.n, 4, mem) if sets else None

@@ -332,8 +332,17 @@ __device__ __forceinline__ void bdec(const BPeel& B, uint32_t u, unsigned long l
     if (old > k && old - c <= k) next[atomicAdd(ncnt, 1u)] = u;
 }
 
+// Lanes of this lane's group when a warp scans 32 / LPR rows at once, LPR
+// lanes each (the intersection tile the launch was tuned with).
+template <int LPR>
+__device__ __forceinline__ unsigned group_mask() {
+    if (LPR == 32) return 0xffffffffu;
+    return ((1u << LPR) - 1u) << (lane_id() & ~(unsigned)(LPR - 1));
+}
+
 // (v, w) item for h >= 3, one warp: the cliques {v, w, ...} whose other
 // members are candidates of v and whose smallest such member is w.
+template <int LPR>
 __device__ unsigned long long bitem(const BPeel& B, uint32_t v, uint32_t w, unsigned long long k,
                                     uint32_t* next, uint32_t* ncnt, uint32_t* C, uint32_t* cnt) {
     unsigned lane = lane_id();
@@ -364,22 +373,25 @@ __device__ unsigned long long bitem(const BPeel& B, uint32_t v, uint32_t w, unsi
         for (uint32_t i = lane; i < nc; i += 32)
             if (B.st[C[i]] == kAl) bdec(B, C[i], 1ull, k, next, ncnt);
     } else {
-        // h = 4: edges of G[C]
+        // h = 4: edges of G[C]; the warp scans 32 / LPR rows at once
         for (uint32_t i = lane; i < nc; i += 32) cnt[i] = 0;
         __syncwarp();
-        for (uint32_t i = 0; i < nc; i++) {
+        const unsigned gl = lane & (LPR - 1), gm = group_mask<LPR>();
+        unsigned long long mine = 0;
+        for (uint32_t i = lane / LPR; i < nc; i += 32 / LPR) {
             uint32_t x = C[i];
             unsigned hits = 0;
-            for (uint32_t p = B.nplus[x] + lane; p < B.off[x + 1]; p += 32) {
+            for (uint32_t p = B.nplus[x] + gl; p < B.off[x + 1]; p += LPR) {
                 uint32_t y = B.adj[p];
                 uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
                 if (pos < nc && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
             }
-            hits = __reduce_add_sync(0xffffffffu, hits);
-            if (lane == 0 && hits) atomicAdd(&cnt[i], hits);
-            tot += hits;
+            hits = __reduce_add_sync(gm, hits);
+            if (gl == 0 && hits) atomicAdd(&cnt[i], hits);
+            if (gl == 0) mine += hits;
         }
         __syncwarp();
+        tot = warp_sum(mine);
         if (tot)
             for (uint32_t i = lane; i < nc; i += 32)
                 if (cnt[i] && B.st[C[i]] == kAl) bdec(B, C[i], cnt[i], k, next, ncnt);
@@ -391,7 +403,7 @@ __device__ unsigned long long bitem(const BPeel& B, uint32_t v, uint32_t w, unsi
 
 // Level-synchronous peel of one graph by one CTA; returns k_max and writes
 // the level records; *nl receives their number.
-template <int NT>
+template <int NT, int LPR>
 __device__ unsigned long long block_peel(const BPeel& B, Smem<NT>& S, uint32_t* nl) {
     constexpr int NW = NT / 32;
     const unsigned lane = lane_id(), wid = warp_id();
@@ -473,7 +485,7 @@ __device__ unsigned long long block_peel(const BPeel& B, Smem<NT>& S, uint32_t* 
             for (uint32_t i = 0; i < nf; i++) {
                 uint32_t v = F[i];
                 for (uint32_t p = B.off[v] + wid; p < B.off[v + 1]; p += NW) {
-                    unsigned long long t = bitem(B, v, B.adj[p], k, G, &S.cnt2, C, cnt);
+                    unsigned long long t = bitem<LPR>(B, v, B.adj[p], k, G, &S.cnt2, C, cnt);
                     if (lane == 0) destroyed += t;
                 }
             }
@@ -506,7 +518,9 @@ __device__ __forceinline__ bool bratio_ge(unsigned long long a, unsigned long lo
 }
 
 // ------------------------------------------------------------ the kernel
-template <int NT>
+// LPR: lanes per row scan (the intersection tile; 32 / LPR rows at once per
+// warp in the triangle listing and the h = 4 edge counts).
+template <int NT, int LPR>
 __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
     constexpr int NW = NT / 32;
     extern __shared__ uint8_t smem_raw[];
@@ -585,7 +599,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
         B2.ls = W.ls;
         B2.mu0 = E / 2;
         uint32_t nl = 0;
-        unsigned long long kmax = block_peel<NT>(B2, S, &nl);
+        unsigned long long kmax = block_peel<NT, LPR>(B2, S, &nl);
         unsigned long long mu = E / 2;
         const unsigned long long* corev = W.core;   // caller ids
         if (D.h >= 3) {
@@ -642,19 +656,24 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
                     __syncwarp();
                     unsigned long long tot = 0;
                     if (D.h == 3) {
-                        // each hit of a row scan is a triangle {u, x, y}
-                        for (uint32_t i = 0; i < d; i++) {
+                        // each hit of a row scan is a triangle {u, x, y}; the
+                        // warp scans 32 / LPR rows at once
+                        const unsigned gl = lane & (LPR - 1), gm = group_mask<LPR>();
+                        unsigned long long mine = 0;
+                        for (uint32_t i = lane / LPR; i < d; i += 32 / LPR) {
                             uint32_t x = C[i];
                             unsigned hits = 0;
-                            for (uint32_t p = W.rsplit[x] + lane; p < W.roff[x + 1]; p += 32) {
+                            for (uint32_t p = W.rsplit[x] + gl; p < W.roff[x + 1]; p += LPR) {
                                 uint32_t y = W.radj[p];
                                 uint32_t pos = (uint32_t)lower_bound_u32(C, d, y);
                                 if (pos < d && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
                             }
-                            hits = __reduce_add_sync(0xffffffffu, hits);
-                            if (lane == 0 && hits) atomicAdd(&cnt[i], hits);
-                            tot += hits;
+                            hits = __reduce_add_sync(gm, hits);
+                            if (gl == 0 && hits) atomicAdd(&cnt[i], hits);
+                            if (gl == 0) mine += hits;
                         }
+                        __syncwarp();
+                        tot = warp_sum(mine);
                     } else if (d <= 32) {
                         // h = 4: triangles of G[C] by the one-word bitmap DFS
                         warp_build_rows32(C, d, W.roff + 1, W.radj, W.rsplit, rows);
@@ -717,7 +736,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs A) {
             B.lm = W.lm;
             B.ls = W.ls;
             B.mu0 = mu;
-            kmax = block_peel<NT>(B, S, &nl);
+            kmax = block_peel<NT, LPR>(B, S, &nl);
             // core numbers back to caller ids (k1 as 64-bit scratch is not
             // needed: write through old_of)
             for (uint32_t i = threadIdx.x; i < n; i += NT) W.deg[W.old_of[i]] = W.core[i];

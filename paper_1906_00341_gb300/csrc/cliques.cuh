@@ -27,30 +27,82 @@ constexpr uint32_t kBitmapMax = 1024;   // candidates per bitmap problem
 // too, and every j > i automatically has C[j] > C[i]; membership is a binary
 // search in C.
 
-// Warp builds one-word rows for |C| <= 32 (rows[i] for i < nc).
+// Row scans read kScanChunks chunks of 32 entries per step (their loads in
+// flight together) and stop at the first chunk past the largest candidate:
+// the lists ascend, so nothing beyond it can be in C.
+constexpr int kScanChunks = 4;
+
+// Hits of the list adj[b, e) (ascending) in the sorted candidates C[0, nc)
+// whose largest entry is cmax, by one warp: cnt[pos] += 1 for each hit
+// (shared counters); returns this lane's number of hits.
+template <class T>
+__device__ __forceinline__ unsigned scan_row_hits(const uint32_t* C, uint32_t nc, uint32_t cmax,
+                                                  const uint32_t* adj, uint64_t b, uint64_t e,
+                                                  T* cnt, uint64_t* read_end = nullptr) {
+    const unsigned lane = lane_id();
+    unsigned hits = 0;
+    uint64_t p0 = b;
+    for (; p0 < e; p0 += 32 * kScanChunks) {
+        uint32_t ys[kScanChunks];
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            ys[u] = p < e ? adj[p] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            const uint32_t y = ys[u];
+            if (y <= cmax) {
+                uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
+                if (pos < nc && C[pos] == y) {
+                    atomicAdd(&cnt[pos], (T)1);
+                    hits++;
+                }
+            }
+        }
+        if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) {
+            p0 += 32 * kScanChunks;
+            break;
+        }
+    }
+    if (read_end) *read_end = p0 < e ? p0 : e;   // entries read: [b, *read_end)
+    return hits;
+}
+
+// Warp builds one-word rows for |C| <= 32 (rows[i] for i < nc).  The last
+// candidate's row is empty (no candidate lies above it).
 template <class OFF>
 __device__ __forceinline__ void warp_build_rows32(const uint32_t* C, uint32_t nc,
                                                   const OFF* ne, const uint32_t* adj,
                                                   const OFF* nb, uint32_t* rows) {
-    unsigned lane = lane_id();
-    for (uint32_t i = 0; i < nc; i++) {
-        uint32_t x = C[i];
-        uint64_t b = nb[x], e = ne[x];
+    const unsigned lane = lane_id();
+    if (nc == 0) return;
+    const uint32_t cmax = C[nc - 1];
+    for (uint32_t i = 0; i + 1 < nc; i++) {
+        const uint32_t x = C[i];
+        const uint64_t b = nb[x], e = ne[x];
         uint32_t bits = 0;
-        for (uint64_t p = b + lane; p - lane < e; p += 32) {
-            bool hit = false;
-            uint32_t pos = 0;
-            if (p < e) {
-                uint32_t y = adj[p];
-                if (y > x) {
-                    pos = (uint32_t)lower_bound_u32(C, nc, y);
-                    hit = pos < nc && C[pos] == y;
+        for (uint64_t p0 = b; p0 < e; p0 += 32 * kScanChunks) {
+            uint32_t ys[kScanChunks];
+#pragma unroll
+            for (int u = 0; u < kScanChunks; u++) {
+                uint64_t p = p0 + u * 32 + lane;
+                ys[u] = p < e ? adj[p] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < kScanChunks; u++) {
+                const uint32_t y = ys[u];
+                if (y > x && y <= cmax) {
+                    uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
+                    if (pos < nc && C[pos] == y) bits |= 1u << pos;
                 }
             }
-            bits |= __reduce_or_sync(0xffffffffu, hit ? (1u << pos) : 0u);
+            if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) break;
         }
+        bits = __reduce_or_sync(0xffffffffu, bits);
         if (lane == 0) rows[i] = bits;
     }
+    if (lane == 0) rows[nc - 1] = 0;
     __syncwarp();
 }
 
@@ -189,16 +241,30 @@ template <class OFF>
 __device__ __forceinline__ void block_build_rows(const uint32_t* C, uint32_t nc, uint32_t W,
                                                  const OFF* ne, const uint32_t* adj,
                                                  const OFF* nb, uint32_t* rows) {
-    unsigned lane = lane_id();
-    unsigned nw = blockDim.x >> 5;
-    for (uint32_t i = warp_id(); i < nc; i += nw) {
-        uint32_t x = C[i];
-        uint64_t b = nb[x], e = ne[x];
-        for (uint64_t p = b + lane; p < e; p += 32) {
-            uint32_t y = adj[p];
-            uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
-            if (pos < nc && C[pos] == y && pos > i)
-                atomicOr(&rows[i * W + (pos >> 5)], 1u << (pos & 31));
+    const unsigned lane = lane_id();
+    const unsigned nw = blockDim.x >> 5;
+    if (nc == 0) return;
+    const uint32_t cmax = C[nc - 1];
+    for (uint32_t i = warp_id(); i + 1 < nc; i += nw) {
+        const uint32_t x = C[i];
+        const uint64_t b = nb[x], e = ne[x];
+        for (uint64_t p0 = b; p0 < e; p0 += 32 * kScanChunks) {
+            uint32_t ys[kScanChunks];
+#pragma unroll
+            for (int u = 0; u < kScanChunks; u++) {
+                uint64_t p = p0 + u * 32 + lane;
+                ys[u] = p < e ? adj[p] : 0xffffffffu;
+            }
+#pragma unroll
+            for (int u = 0; u < kScanChunks; u++) {
+                const uint32_t y = ys[u];
+                if (y > x && y <= cmax) {
+                    uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
+                    if (pos < nc && C[pos] == y && pos > i)
+                        atomicOr(&rows[i * W + (pos >> 5)], 1u << (pos & 31));
+                }
+            }
+            if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) break;
         }
     }
 }

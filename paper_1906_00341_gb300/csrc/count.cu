@@ -75,15 +75,10 @@ __global__ void __launch_bounds__(kCountThreads) k_count_small(CountArgs A) {
             if (A.r == 2) {
                 // triangles: hits of row i are the third members
                 unsigned long long t = 0;
-                for (uint32_t i = 0; i < d; i++) {
+                const uint32_t cmax = C[d - 1];
+                for (uint32_t i = 0; i + 1 < d; i++) {
                     uint32_t x = C[i];
-                    uint64_t xb = A.split[x], xe = A.off[x + 1];
-                    unsigned hits = 0;
-                    for (uint64_t p = xb + lane; p < xe; p += 32) {
-                        uint32_t y = A.adj[p];
-                        uint32_t pos = (uint32_t)lower_bound_u32(C, d, y);
-                        if (pos < d && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
-                    }
+                    unsigned hits = scan_row_hits(C, d, cmax, A.adj, A.split[x], A.off[x + 1], cnt);
                     hits = __reduce_add_sync(0xffffffffu, hits);
                     if (lane == 0 && hits) { atomicAdd(&cnt[i], hits); }
                     t += hits;
@@ -135,15 +130,10 @@ __global__ void __launch_bounds__(NT) k_count_medium(CountArgs A) {
         unsigned long long mine = 0;
         if (A.r == 2) {
             unsigned lane = lane_id(), nw = blockDim.x >> 5;
-            for (uint32_t i = warp_id(); i < d; i += nw) {
+            const uint32_t cmax = C[d - 1];
+            for (uint32_t i = warp_id(); i + 1 < d; i += nw) {
                 uint32_t x = C[i];
-                uint64_t xb = A.split[x], xe = A.off[x + 1];
-                unsigned hits = 0;
-                for (uint64_t p = xb + lane; p < xe; p += 32) {
-                    uint32_t y = A.adj[p];
-                    uint32_t pos = (uint32_t)lower_bound_u32(C, d, y);
-                    if (pos < d && C[pos] == y) { atomicAdd(&cnt[pos], 1ull); hits++; }
-                }
+                unsigned hits = scan_row_hits(C, d, cmax, A.adj, A.split[x], A.off[x + 1], cnt);
                 hits = __reduce_add_sync(0xffffffffu, hits);
                 if (lane == 0 && hits) atomicAdd(&cnt[i], (unsigned long long)hits);
                 if (lane == 0) mine += hits;

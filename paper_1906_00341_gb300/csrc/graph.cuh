@@ -106,7 +106,9 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
                     const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
                     uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
                     uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res,
-                    uint64_t kstart = 0);
+                    uint64_t kstart = 0, uint64_t* snap = nullptr);
+// snap (may be null; no cluster tail then): snap[v] receives v's count in
+// R_core(v), its clique-degree inside its own (k,Psi)-core.
 // kstart > 0: the first level removes every vertex with fewer than kstart
 // cliques in one cascade (threshold pruning to the (kstart,Psi)-core); its
 // level record is then (kstart - 1, |V|, mu) and the core numbers it assigns

@@ -62,6 +62,8 @@ constexpr int kChunks = 4;              // 32-entry chunks of a row in flight pe
 constexpr uint32_t kWarpCand = 32;      // candidate sets a warp handles itself (h >= 4)
 constexpr uint32_t kWarpWords = 3 * kWarpCand;   // a warp's candidates, counters, rows
 constexpr uint32_t kHeavyBit = 4;       // state word: frontier vertex on the heavy list
+constexpr uint32_t kSlotShift = 3;      // state word: 1 + its neighbourhood bitmap slot
+constexpr uint32_t kSlotMask = 0xffu;
 
 __device__ __forceinline__ uint32_t st_of(uint32_t w) { return w & 3u; }
 
@@ -73,7 +75,9 @@ struct PeelCtrl {
     unsigned long long destroyed[3];
     uint32_t hcnt[3];               // heavy frontier vertices of the round
     uint32_t grab[3];               // light frontier vertices taken by blocks
-    uint32_t pad0[10];
+    uint32_t bgrab[3];              // big items taken by blocks
+    uint32_t hubcnt[2];             // bitmap slots asked for, by round parity
+    uint32_t pad0[5];
     uint32_t bar_count;
     uint32_t pad1[31];
     uint32_t bar_gen;
@@ -132,6 +136,16 @@ struct PeelParams {
     uint64_t big_cap;
     uint32_t* heavy;       // large regime: frontier vertices with long rows
     uint32_t heavy_min;    // rows longer than this are heavy (0 = no heavy list)
+    // Large regime: frontier vertices with rows longer than hub_min get (up
+    // to hub_slots per round) a bitmap of their neighbourhood over vertex
+    // ids, so that "x in N(v)" is one probe instead of a binary search.  Two
+    // sets of hub_slots bitmaps of hub_words words, by round parity; hubs
+    // lists the owners (2 x hub_slots).
+    uint32_t* hub_bm;
+    uint32_t* hubs;
+    uint64_t hub_words;
+    uint32_t hub_slots;    // 0 = no bitmaps
+    uint32_t hub_min;
     uint64_t* lvl_k;
     uint32_t* lvl_size;
     uint64_t* lvl_mu;
@@ -144,6 +158,8 @@ struct PeelParams {
     uint32_t work_words;   // shared words before the small-regime lists
     uint32_t asmall;       // small-regime list capacity (0 = regime off)
     uint32_t tail_max;     // hand over to the cluster tail at <= this many alive (0 = off)
+    uint64_t* snap;        // if set: each alive vertex's count at every level jump (the
+                           // last one written is its count in its own (k,Psi)-core)
 };
 
 // ------------------------------------------------------------ barrier
@@ -288,10 +304,10 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
 //   kGatherDirect (h = 3): each candidate closes the triangle {v, w, x}; an
 //     alive candidate loses it on the spot; nothing is stored;
 //   kGatherWarp: the first kWarpCand candidates go to C; the walk stops as
-//     soon as there are more (the item then needs a block);
-//   kGatherAll: every candidate goes to C (capacity P.cap).
+//     soon as there are more (the item then needs a block).
+// gbm (large regime, may be null): v's neighbourhood bitmap over vertex ids.
 // Returns the number of candidates seen.
-enum { kGatherDirect = 0, kGatherWarp = 1, kGatherAll = 2 };
+enum { kGatherDirect = 0, kGatherWarp = 1 };
 
 template <int MODE>
 __device__ __forceinline__ void take_candidate(const PeelParams& P, bool ok, bool alive,
@@ -307,7 +323,7 @@ __device__ __forceinline__ void take_candidate(const PeelParams& P, bool ok, boo
         }
     } else {
         uint32_t at = nc + __popc(bal & ((1u << lane) - 1u));
-        if (ok && (MODE == kGatherAll || at < kWarpCand)) C[at] = x;
+        if (ok && at < kWarpCand) C[at] = x;
     }
     nc += __popc(bal);
 }
@@ -315,7 +331,8 @@ __device__ __forceinline__ void take_candidate(const PeelParams& P, bool ok, boo
 template <int MODE>
 __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint32_t v,
                                                       uint32_t w, uint32_t* C,
-                                                      const uint32_t* bm, unsigned long long k,
+                                                      const uint32_t* bm, const uint32_t* gbm,
+                                                      unsigned long long k,
                                                       uint32_t* next, uint32_t* next_cnt,
                                                       unsigned long long& bytes) {
     unsigned lane = lane_id();
@@ -327,7 +344,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
     uint32_t nc = 0;
     // Walk the shorter side: the entries of N(v) above w, each searched in
     // N+(w), when that costs fewer probes than walking N+(w).
-    const uint64_t cost_w = bm ? dw : dw * pr;
+    const uint64_t cost_w = (bm || gbm) ? dw : dw * pr;
     if (dv * probes(dw) < cost_w) {
         const uint32_t* Nw = P.wadj + b;
         uint64_t s0 = lower_bound_u32(Nv, dv, w + 1u);
@@ -388,6 +405,9 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
                     if (bm) {
                         uint32_t l = ws[u] >> 2;
                         ok = (bm[l >> 5] >> (l & 31)) & 1u;
+                    } else if (gbm) {
+                        ok = (gbm[x >> 5] >> (x & 31)) & 1u;
+                        bytes += 4;
                     } else {
                         uint64_t pos = lower_bound_u32(Nv, dv, x);
                         ok = pos < dv && Nv[pos] == x;
@@ -410,7 +430,8 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
                            uint32_t* rows, uint32_t* big_cnt, const uint32_t* bm,
-                           unsigned long long& destroyed, unsigned long long& bytes) {
+                           const uint32_t* gbm, unsigned long long& destroyed,
+                           unsigned long long& bytes) {
     unsigned lane = lane_id();
     uint32_t sw = st_of(P.sl[w]);
     if (lane == 0) bytes += 4 + 4;   // w, its state word
@@ -419,9 +440,10 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
     const int r = P.h - 2;
     unsigned long long tot = 0;
     if (r == 1) {
-        tot = gather_candidates<kGatherDirect>(P, v, w, C, bm, k, next, next_cnt, bytes);
+        tot = gather_candidates<kGatherDirect>(P, v, w, C, bm, gbm, k, next, next_cnt, bytes);
     } else {
-        uint32_t nc = gather_candidates<kGatherWarp>(P, v, w, C, bm, k, next, next_cnt, bytes);
+        uint32_t nc =
+            gather_candidates<kGatherWarp>(P, v, w, C, bm, gbm, k, next, next_cnt, bytes);
         __syncwarp();
         if (nc < (uint32_t)r) return;
         if (nc > kWarpCand) {
@@ -436,17 +458,12 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         __syncwarp();
         if (r == 2) {
             // edges of G[C]: each is a clique {v, w, x, y}
-            for (uint32_t i = 0; i < nc; i++) {
+            const uint32_t cmax = C[nc - 1];
+            for (uint32_t i = 0; i + 1 < nc; i++) {
                 uint32_t x = C[i];
-                uint64_t xb = P.wnb[x], xe = P.wend[x];
-                unsigned hits = 0;
-                if (lane == 0) bytes += 16;
-                for (uint64_t p = xb + lane; p < xe; p += 32) {
-                    uint32_t y = P.wadj[p];
-                    bytes += 4;
-                    uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
-                    if (pos < nc && C[pos] == y) { atomicAdd(&cnt[pos], 1u); hits++; }
-                }
+                uint64_t xb = P.wnb[x], xe = P.wend[x], xr = xe;
+                unsigned hits = scan_row_hits(C, nc, cmax, P.wadj, xb, xe, cnt, &xr);
+                if (lane == 0) bytes += 16 + 4ull * (xr - xb);
                 hits = __reduce_add_sync(0xffffffffu, hits);
                 if (lane == 0 && hits) atomicAdd(&cnt[i], hits);
                 tot += hits;
@@ -485,22 +502,71 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
 // bitmap rows of G[C] and a warp-level DFS per starting candidate.
 __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                             uint32_t* next, uint32_t* next_cnt, uint32_t* smem,
-                            unsigned long long& destroyed, unsigned long long& bytes) {
+                            const uint32_t* gbm, unsigned long long& destroyed,
+                            unsigned long long& bytes) {
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // cap
     uint32_t* C = smem + 2 * P.cap;                                           // cap
     uint32_t* rows = C + P.cap;                                               // cap * W
     __shared__ uint32_t s_nc;
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_tot;
+    __shared__ uint32_t s_flag[kBitmapMax / 32], s_at[kBitmapMax / 32];
+    const unsigned lane = lane_id(), nw = blockDim.x >> 5;
     uint32_t sw = st_of(P.sl[w]);
+    // candidates of v among N+(w), all warps at once: warp c tests the c-th
+    // run of 32 entries, the runs' hit masks are compacted in order
+    const uint64_t b = P.wnb[w], e = P.wend[w];
+    const uint32_t runs = (uint32_t)((e - b + 31) >> 5);   // <= kBitmapMax / 32
+    const uint32_t* Nv = P.wadj + P.off[v];
+    const uint64_t dv = P.wend[v] - P.off[v];
+    const unsigned pr = probes(dv);
+    for (uint32_t c = warp_id(); c < runs; c += nw) {
+        const uint64_t p = b + (uint64_t)c * 32 + lane;
+        bool ok = false;
+        if (p < e) {
+            const uint32_t x = P.wadj[p];
+            const uint32_t st = st_of(P.sl[x]);
+            bytes += 8;
+            if (st == kAlive || (st == kFront && x > v)) {
+                if (gbm) {
+                    ok = (gbm[x >> 5] >> (x & 31)) & 1u;
+                    bytes += 4;
+                } else {
+                    uint64_t pos = lower_bound_u32(Nv, dv, x);
+                    ok = pos < dv && Nv[pos] == x;
+                    bytes += 4ull * pr;
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (lane == 0) s_flag[c] = bal;
+    }
+    __syncthreads();
     if (warp_id() == 0) {
-        uint32_t nc = gather_candidates<kGatherAll>(P, v, w, C, nullptr, k, next, next_cnt, bytes);
-        if (lane_id() == 0) {
-            s_nc = nc;
+        uint32_t tot = 0;
+        for (uint32_t c0 = 0; c0 < runs; c0 += 32) {
+            const uint32_t c = c0 + lane;
+            uint32_t x = c < runs ? (uint32_t)__popc(s_flag[c]) : 0u, inc = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            if (c < runs) s_at[c] = tot + inc - x;
+            tot += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) {
+            s_nc = tot;
             s_next = 0;
             s_tot = 0;
             bytes += 4 + 4 + 16;
         }
+    }
+    __syncthreads();
+    for (uint32_t c = warp_id(); c < runs; c += nw) {
+        const unsigned bal = s_flag[c];
+        if ((bal >> lane) & 1u)
+            C[s_at[c] + __popc(bal & ((1u << lane) - 1u))] = P.wadj[b + (uint64_t)c * 32 + lane];
     }
     __syncthreads();
     uint32_t nc = s_nc;
@@ -564,6 +630,63 @@ __device__ __forceinline__ void compact_row(const PeelParams& P, uint32_t v,
     }
 }
 
+// Large regime: the neighbourhood bitmap of frontier vertex v for rounds of
+// parity par, or null if v has none.
+__device__ __forceinline__ const uint32_t* hub_bm_of(const PeelParams& P, uint32_t v,
+                                                    uint32_t par) {
+    if (!P.hub_slots) return nullptr;
+    uint32_t slot = (P.sl[v] >> kSlotShift) & kSlotMask;
+    return slot ? P.hub_bm + ((size_t)par * P.hub_slots + (slot - 1)) * P.hub_words : nullptr;
+}
+
+// Large regime, marking v as a member of frontier F_r: its state word, with
+// kHeavyBit for rows longer than heavy_min and, for rows longer than hub_min
+// while slots of this parity last, 1 + its bitmap slot (the owner goes to
+// the parity's hub list).
+__device__ __forceinline__ uint32_t front_word(const PeelParams& P, PeelCtrl* c, uint32_t v,
+                                               uint32_t par, bool& hv) {
+    uint64_t d = P.wend[v] - P.off[v];
+    hv = P.heavy_min && d > P.heavy_min;
+    uint32_t w = kFront | (hv ? kHeavyBit : 0u);
+    if (hv && P.hub_slots && d > P.hub_min) {
+        uint32_t at = atomicAdd(&c->hubcnt[par], 1u);
+        if (at < P.hub_slots) {
+            P.hubs[par * P.hub_slots + at] = v;
+            w |= (at + 1u) << kSlotShift;
+        }
+    }
+    return w;
+}
+
+// Sets (or, clear = true, zeroes the words of) the bitmaps of the hubs of
+// parity par over their rows; the rows' entries are flattened over every
+// thread of the grid.  Every thread of every block calls it.
+template <int NT>
+__device__ __forceinline__ void hub_bitmaps(const PeelParams& P, uint32_t nhub, uint32_t par,
+                                            bool clear, unsigned long long* s_pre,
+                                            unsigned long long* s_red,
+                                            unsigned long long& bytes) {
+    const uint32_t* H = P.hubs + (size_t)par * P.hub_slots;
+    block_prefix_degrees<NT>(P, H, nhub, s_pre, s_red);
+    const unsigned long long T = s_pre[nhub];
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = gtid; t < T; t += gthreads) {
+        uint32_t lo = 0, hi = nhub;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (s_pre[mid] <= t) lo = mid; else hi = mid;
+        }
+        uint32_t v = H[lo];
+        uint32_t x = P.wadj[P.off[v] + (t - s_pre[lo])];
+        uint32_t* bm = P.hub_bm + ((size_t)par * P.hub_slots + lo) * P.hub_words;
+        if (clear) bm[x >> 5] = 0u;   // every set bit belongs to a row entry
+        else atomicOr(&bm[x >> 5], 1u << (x & 31));
+        bytes += 4 + 16;
+    }
+    __syncthreads();   // s_pre is reused afterwards
+}
+
 // P2: the cliques destroyed by frontier F (nf vertices; F in global or
 // shared memory, identical for every block).  bm: shared bitmaps of the
 // neighbourhoods of F[0 .. min(nf, kBitmapSlots)) (small regime), or null.
@@ -572,7 +695,7 @@ __device__ __forceinline__ void process_frontier(
     const PeelParams& P, const uint32_t* F, uint32_t nf, unsigned long long k, uint32_t* Fnext,
     uint32_t* next_cnt, uint32_t* big_cnt, uint32_t* wC, unsigned* wCnt, uint32_t* wRows,
     const uint32_t* bm, uint32_t bm_words, unsigned long long* s_pre, unsigned long long* s_red,
-    const uint32_t* hl, uint32_t nh, uint32_t* grab, uint32_t* s_grab,
+    const uint32_t* hl, uint32_t nh, uint32_t* grab, uint32_t* s_grab, uint32_t par,
     unsigned long long& destroyed, unsigned long long& items, unsigned long long& bytes) {
     constexpr int NW = NT / 32;
     const unsigned lane = lane_id(), wid = warp_id();
@@ -617,8 +740,9 @@ __device__ __forceinline__ void process_frontier(
                 uint32_t v = F[lo];
                 uint32_t w = P.wadj[P.off[v] + (t - s_pre[lo])];
                 const uint32_t* vbm = (bm && lo < kBitmapSlots) ? bm + (size_t)lo * bm_words : nullptr;
-                process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, vbm, destroyed,
-                           bytes);
+                const uint32_t* gbm = hl ? hub_bm_of(P, v, par) : nullptr;
+                process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, vbm, gbm,
+                           destroyed, bytes);
             }
         }
     } else if (P.h == 2) {
@@ -667,7 +791,7 @@ __device__ __forceinline__ void process_frontier(
                     uint32_t v = H[lo];
                     uint32_t w = P.wadj[P.off[v] + (t - s_pre[lo])];
                     process_vw(P, v, w, k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, nullptr,
-                               destroyed, bytes);
+                               hub_bm_of(P, v, par), destroyed, bytes);
                 }
                 __syncthreads();   // s_pre is rewritten by the next batch
             }
@@ -686,7 +810,7 @@ __device__ __forceinline__ void process_frontier(
                     uint64_t b = P.off[v], e = P.wend[v];
                     for (uint64_t p = b + wid; p < e; p += NW)
                         process_vw(P, v, P.wadj[p], k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt,
-                                   nullptr, destroyed, bytes);
+                                   nullptr, nullptr, destroyed, bytes);
                     if (threadIdx.x == 0) {
                         items += e - b;
                         bytes += 24;
@@ -701,7 +825,7 @@ __device__ __forceinline__ void process_frontier(
             const uint32_t* vbm = (bm && i < kBitmapSlots) ? bm + (size_t)i * bm_words : nullptr;
             for (uint64_t p = b + wid; p < e; p += NW)
                 process_vw(P, v, P.wadj[p], k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt, vbm,
-                           destroyed, bytes);
+                           nullptr, destroyed, bytes);
             if (threadIdx.x == 0) {
                 items += e - b;
                 bytes += 20;
@@ -812,6 +936,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             }
             uint32_t fcur = c->fcnt[r % 3];
             uint32_t* Fcur = P.front[r % 3];
+            // the bitmaps of F_{r-1}'s hubs are zeroed for round r+1
+            if (r && P.hub_slots) {
+                uint32_t nhub = c->hubcnt[(r + 1) & 1];
+                if (nhub > P.hub_slots) nhub = P.hub_slots;
+                if (nhub) hub_bitmaps<NT>(P, nhub, (r + 1) & 1, true, s_pre, s_red, bytes);
+            }
             // mark F_r; rows longer than heavy_min also go to the heavy list
             for (uint64_t base = gwarp * 32; base < fcur; base += gwarps * 32) {
                 uint64_t i = base + lane;
@@ -819,8 +949,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 uint32_t v = 0;
                 if (i < fcur) {
                     v = Fcur[i];
-                    hv = P.heavy_min && P.wend[v] - P.off[v] > P.heavy_min;
-                    P.sl[v] = kFront | (hv ? kHeavyBit : 0u);
+                    P.sl[v] = P.heavy_min ? front_word(P, c, v, r & 1, hv) : (uint32_t)kFront;
                     bytes += 4 + 4 + (P.heavy_min ? 16 : 0);
                 }
                 if (P.heavy_min) warp_append(hv, v, &c->hcnt[r % 3], P.heavy);
@@ -830,6 +959,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     mu_alive -= c->destroyed[(r + 2) % 3];
                     c->destroyed[(r + 2) % 3] = 0;
                     c->big_cnt[(r + 2) % 3] = 0;
+                    c->bgrab[(r + 2) % 3] = 0;
                 }
                 c->fcnt[(r + 1) % 3] = 0;
                 c->hcnt[(r + 1) % 3] = 0;
@@ -853,6 +983,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                             keep = true;
                             unsigned long long d = P.deg[v];
                             mn = d < mn ? d : mn;
+                            if (P.snap) P.snap[v] = d;
                             bytes += 8 + 4;
                         }
                     }
@@ -916,8 +1047,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                             bytes += 4 + 8;
                             if (P.deg[v] <= k) {
                                 in = true;
-                                hv = P.heavy_min && P.wend[v] - P.off[v] > P.heavy_min;
-                                P.sl[v] = kFront | (hv ? kHeavyBit : 0u);
+                                P.sl[v] = P.heavy_min ? front_word(P, c, v, r & 1, hv)
+                                                      : (uint32_t)kFront;
                                 bytes += 4 + 4 + (P.heavy_min ? 16 : 0);
                             }
                         }
@@ -930,12 +1061,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             }
             if (!small) {
                 // -------------------------------------------------- P2
+                if (P.hub_slots) {
+                    uint32_t nhub = c->hubcnt[r & 1];
+                    if (nhub > P.hub_slots) nhub = P.hub_slots;
+                    if (lead) c->hubcnt[(r + 1) & 1] = 0;   // read last in this round's P1
+                    if (nhub) {
+                        hub_bitmaps<NT>(P, nhub, r & 1, false, s_pre, s_red, bytes);
+                        BARRIER(3);
+                    }
+                }
                 unsigned long long destroyed = 0;
                 process_frontier<NT>(P, Fcur, fcur, k, P.front[(r + 1) % 3],
                                      &c->fcnt[(r + 1) % 3], &c->big_cnt[r % 3], wC, wCnt,
                                      wRows, nullptr, 0, s_pre, s_red,
                                      P.heavy_min ? P.heavy : nullptr, c->hcnt[r % 3],
-                                     &c->grab[r % 3], &s_grab, destroyed, items, bytes);
+                                     &c->grab[r % 3], &s_grab, r & 1, destroyed, items, bytes);
                 unsigned long long bd = block_sum<NT>(destroyed, s_red);
                 if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
                 BARRIER(3);
@@ -945,10 +1085,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     if (nb) {
                         if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
                         unsigned long long d2 = 0;
-                        for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+                        for (;;) {
+                            if (threadIdx.x == 0) s_grab = atomicAdd(&c->bgrab[r % 3], 1u);
+                            __syncthreads();
+                            const uint32_t i = s_grab;
+                            __syncthreads();
+                            if (i >= nb) break;
                             uint2 it = P.big[i];
                             process_big(P, it.x, it.y, k, P.front[(r + 1) % 3],
-                                        &c->fcnt[(r + 1) % 3], smem, d2, bytes);
+                                        &c->fcnt[(r + 1) % 3], smem, hub_bm_of(P, it.x, r & 1),
+                                        d2, bytes);
                         }
                         if (threadIdx.x == 0 && d2) atomicAdd(&c->destroyed[r % 3], d2);
                         BARRIER(3);
@@ -973,6 +1119,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 mu_alive -= c->destroyed[(r + 2) % 3];
                 c->destroyed[(r + 2) % 3] = 0;
                 c->big_cnt[(r + 2) % 3] = 0;
+                c->bgrab[(r + 2) % 3] = 0;
             }
             uint32_t nf_new = c->fcnt[r % 3];
             __syncthreads();
@@ -1007,6 +1154,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     unsigned long long d = i < na_loc ? P.deg[v] : ~0ull;
                     bool keep = s == kAlive;
                     if (keep) lmin = d < lmin ? d : lmin;
+                    if (keep && P.snap) P.snap[v] = d;
                     uint32_t tot;
                     uint32_t at = block_scan_count<NT>(keep ? 1u : 0u, s_wtot, &tot);
                     uint32_t o = s_n;
@@ -1149,8 +1297,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             unsigned long long destroyed = 0;
             process_frontier<NT>(P, sF, nf_s, k, P.front[(r + 1) % 3], &c->fcnt[(r + 1) % 3],
                                  &c->big_cnt[r % 3], wC, wCnt, wRows, P.h >= 3 ? sBM : nullptr,
-                                 bm_words, s_pre, s_red, nullptr, 0, nullptr, nullptr, destroyed,
-                                 items, bytes);
+                                 bm_words, s_pre, s_red, nullptr, 0, nullptr, nullptr, 0,
+                                 destroyed, items, bytes);
             unsigned long long bd = block_sum<NT>(destroyed, s_red);
             if (threadIdx.x == 0 && bd) atomicAdd(&c->destroyed[r % 3], bd);
             BARRIER(7);
@@ -1159,10 +1307,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 if (nb) {
                     if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
                     unsigned long long d2 = 0;
-                    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+                    for (;;) {
+                        if (threadIdx.x == 0) s_grab = atomicAdd(&c->bgrab[r % 3], 1u);
+                        __syncthreads();
+                        const uint32_t i = s_grab;
+                        __syncthreads();
+                        if (i >= nb) break;
                         uint2 it = P.big[i];
                         process_big(P, it.x, it.y, k, P.front[(r + 1) % 3],
-                                    &c->fcnt[(r + 1) % 3], smem, d2, bytes);
+                                    &c->fcnt[(r + 1) % 3], smem, nullptr, d2, bytes);
                     }
                     if (threadIdx.x == 0 && d2) atomicAdd(&c->destroyed[r % 3], d2);
                     BARRIER(7);
@@ -1329,7 +1482,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
                     const uint64_t* split, uint32_t maxdplus, unsigned long long* deg,
                     uint64_t mu0, uint64_t* core, uint32_t* rnd, uint64_t* lvl_k,
                     uint32_t* lvl_size, uint64_t* lvl_mu, PeelResult* res,
-                    uint64_t kstart) {
+                    uint64_t kstart, uint64_t* snap) {
     cudaStream_t s = g->stream;
     *res = PeelResult();
     if (n == 0) return DSD_OK;
@@ -1349,6 +1502,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.wait_ns = wait_limit_ns();
     P.mu0 = mu0;
     P.k0 = kstart ? kstart - 1 : 0;
+    P.snap = snap;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
     P.compact = h >= 3 ? 1 : 0;
     if (h >= 4 && maxdplus > kBitmapMax) {
@@ -1368,6 +1522,15 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     // large-regime frontier vertices with more items than a block's warps
     // take in four passes have their items spread over the whole grid
     P.heavy_min = h >= 3 ? 4u * (NT / 32) : 0u;
+    // neighbourhood bitmaps for frontier vertices with rows above 512 (a
+    // binary search there takes 10 or more probes): up to 64 per round, two
+    // sets, within 64 MiB
+    if (h >= 3) {
+        P.hub_words = ((uint64_t)n + 31) / 32;
+        uint64_t slots = (64ull << 20) / (2 * 4 * P.hub_words);
+        P.hub_slots = (uint32_t)(slots > 64 ? 64 : (slots < 4 ? 0 : slots));
+        P.hub_min = 4 * P.heavy_min;
+    }
     if (big_items) {
         size_t W = (P.cap + 31) / 32;
         size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
@@ -1386,7 +1549,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.work_words = (uint32_t)work;
     P.asmall = (uint32_t)asmall;
     TailShape tsh_d, tsh_g;   // rows in distributed shared memory / in global memory
-    if ((h == 2 || h == 3) && asmall > 0 && peel_tail_limit() > 0) {
+    if ((h == 2 || h == 3) && asmall > 0 && peel_tail_limit() > 0 && !snap) {
         tsh_d = tail_shape(false);
         // global rows pay for h = 3 only: an h = 2 round is too cheap for the
         // wider rows (measured on the 1M-vertex Chung-Lu graph)
@@ -1407,6 +1570,8 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     uint32_t* rows_g = nullptr;
     uint2* big = nullptr;
     uint32_t* heavy = nullptr;
+    uint32_t* hub_bm = nullptr;
+    uint32_t* hubs = nullptr;
     ulonglong2* jblk = nullptr;
     dsd_status st = DSD_OK;
     PeelCtrl hc;
@@ -1428,6 +1593,17 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     }
     if (P.heavy_min && (st = dalloc(&heavy, n, s)) != DSD_OK) goto done;
     P.heavy = heavy;
+    if (P.hub_slots) {
+        if ((st = dalloc(&hub_bm, (size_t)2 * P.hub_slots * P.hub_words, s)) != DSD_OK) goto done;
+        if ((st = dalloc(&hubs, (size_t)2 * P.hub_slots, s)) != DSD_OK) goto done;
+        e = cudaMemsetAsync(hub_bm, 0, (size_t)2 * P.hub_slots * P.hub_words * 4, s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "peel bitmaps", __FILE__, __LINE__);
+            goto done;
+        }
+    }
+    P.hub_bm = hub_bm;
+    P.hubs = hubs;
     P.sl = sl;
     P.alive[0] = lists;
     P.alive[1] = lists + n;
@@ -1527,6 +1703,8 @@ done:
     dev_free(rows_g, s);
     dev_free(big, s);
     dev_free(heavy, s);
+    dev_free(hub_bm, s);
+    dev_free(hubs, s);
     dev_free(jblk, s);
     return st;
 }

@@ -10,13 +10,17 @@
 // j >= k, R_j(H) = R_j(G) because R_j(G) is the largest vertex set with the
 // property and lies in H.
 //
-// Acceptance: R_k non-empty and rho(R_k) >= rho' (exact: rho' is a float
-// M 2^E, compared as integers).  Then every level j < k has density at most
-// max(rho(R_{j+1}), j) <= ... <= max(rho(R_k), k - 1) (each vertex removed at
-// level j destroys at most j cliques), and k - 1 < rho' <= rho(R_k), so the
-// densest level (ties to the larger k), k_max and the k_max core are all
-// found among the levels >= k (Lemma 5 gives the same containment for the
-// optimum).  A rejected proposal falls back to the plain decomposition.
+// Acceptance: some level is >= k and the densest level >= k has density at
+// least k - 1 (128-bit integers).  Every level j < k has density at most
+// max(rho(R_{j+1}), j) <= ... <= max(rho(R_k), k - 1) (each vertex removed
+// at level j destroys at most j cliques), which the densest level >= k then
+// reaches, so the densest level (ties to the larger k), k_max and the k_max
+// core are all found among the levels >= k (Lemma 5 gives the same
+// containment for the optimum).  Every proposal rho' <= rho(S*) passes: the
+// densest level's k is at least its density (a level denser than its own k
+// is beaten or tied by the next, Theorem 1 bounds the last by k_max), so
+// k = ceil(rho') does not exceed it.  A rejected proposal falls back to the
+// plain decomposition.
 #include "graph.cuh"
 
 #include <math.h>
@@ -104,41 +108,30 @@ struct SeedRes {
     uint32_t kmax_core_size, densest_size, nlevels, accepted;
 };
 
-// mu / size >= M * 2^E (M, E of rho'), in 128-bit integers.
-__device__ bool dens_ge(unsigned long long mu, unsigned long long size, unsigned long long Mn,
-                        int E) {
-    unsigned __int128 lhs = mu, rhs = (unsigned __int128)Mn * size;
-    if (E >= 0) {
-        if (E >= 64) return Mn == 0;
-        rhs <<= E;
-    } else {
-        int s = -E;
-        if (s >= 64) return true;
-        lhs <<= s;
-    }
-    return lhs >= rhs;
-}
-
 __device__ __forceinline__ bool ratio_ge2(unsigned long long a, unsigned long long b,
                                           unsigned long long c, unsigned long long d) {
     unsigned __int128 l = (unsigned __int128)a * d, r = (unsigned __int128)c * b;
     return l >= r;
 }
 
-// Among the levels >= k: R_k (the first), the densest (ties to the larger
-// k) and the last.  One thread; the level count is small.
+// Among the levels >= k: the densest (ties to the larger k) and the last.
+// Accepted iff a level >= k exists and that densest one has density at
+// least k - 1: every level j < k then has density at most max(rho(R_k),
+// k - 1) (each vertex leaving at level j holds at most j cliques when it
+// leaves), so no lower level beats it and the answer lies among the levels
+// >= k.  One thread; the level count is small.
 __global__ void k_seed_select(uint32_t nl, const uint64_t* lk, const uint32_t* ls,
-                              const uint64_t* lm, unsigned long long k, unsigned long long Mn,
-                              int E, SeedRes* out) {
+                              const uint64_t* lm, unsigned long long k, SeedRes* out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     SeedRes r;
     memset(&r, 0, sizeof(r));
     uint32_t j0 = 0;
     while (j0 < nl && lk[j0] < k) j0++;
-    if (j0 < nl && dens_ge(lm[j0], ls[j0], Mn, E)) {
-        uint32_t best = j0;
-        for (uint32_t j = j0 + 1; j < nl; j++)
-            if (ratio_ge2(lm[j], ls[j], lm[best], ls[best])) best = j;
+    uint32_t best = j0;
+    for (uint32_t j = j0 + 1; j < nl; j++)
+        if (ratio_ge2(lm[j], ls[j], lm[best], ls[best])) best = j;
+    // rho(R_best) >= k - 1  <=>  mu >= (k - 1) * |R_best|  (128-bit)
+    if (j0 < nl && ratio_ge2(lm[best], ls[best], k - 1, 1)) {
         r.accepted = 1;
         r.kmax = lk[nl - 1];
         r.kmax_core_size = ls[nl - 1];
@@ -397,10 +390,6 @@ dsd_status dsd_core_app_seeded_info(dsd_graph* g, int h, const dsd_model* Mc,
         if (x0 > g->degeneracy) try_seed = false;   // no vertex can reach level k
     }
     if (try_seed) {
-        int Eexp = 0;
-        float mant = frexpf(rho, &Eexp);            // rho = mant * 2^Eexp, mant in [0.5, 1)
-        unsigned long long Mn = (unsigned long long)ldexpf(mant, 24);
-        int E = Eexp - 24;
         SubCore S;
         SeedRes hs;
         memset(&hs, 0, sizeof(hs));
@@ -413,7 +402,7 @@ dsd_status dsd_core_app_seeded_info(dsd_graph* g, int h, const dsd_model* Mc,
             st = dalloc(&sr, 1, s);
         }
         if (st == DSD_OK) {
-            k_seed_select<<<1, 32, 0, s>>>(S.pr.nlevels, S.lk, S.ls, S.lm, k, Mn, E, sr);
+            k_seed_select<<<1, 32, 0, s>>>(S.pr.nlevels, S.lk, S.ls, S.lm, k, sr);
             note_launch();
             cudaError_t e = cudaMemcpyAsync(&hs, sr, sizeof(hs), cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);

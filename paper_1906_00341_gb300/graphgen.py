@@ -331,3 +331,38 @@ def train_graph(i: int, nmax: int = 200000, nmedian: float = 3000.0):
                                    exclude=used)
             used.extend(verts.tolist())
     return n, s, d, 3
+
+
+# ---------------------------------------------------------------------------
+# Large graphs shaped like the cl4m workload: 16 n Chung-Lu endpoint draws,
+# exponent U[2.1, 2.4], maximum expected degree sqrt(32 n), plus 1-5 planted
+# G(k, U[0.3, 0.5]) blocks on disjoint vertices, k uniform in 150..300,
+# n = round(exp(U[ln nmin, ln nmax])); clique size h = 3.
+#   held-out evaluation graph i: seed splitmix64(3,000,000 + i), n in
+#     [200,000, 4,000,000], never used in training;
+#   large training graph i: seed splitmix64(4,000,000 + i), n in
+#     [100,000, 2,000,000].
+# Both seed ranges are disjoint from each other, from the small training
+# graphs, the batches and the named workloads.
+# ---------------------------------------------------------------------------
+
+def _cl_blocks_graph(seed: int, nmin: int, nmax: int):
+    rng = np.random.default_rng(seed)
+    n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+    beta = float(rng.uniform(2.1, 2.4))
+    draws = 16 * n
+    sub = int(rng.integers(0, 2**31))
+    blocks = [(int(rng.integers(150, 301)), float(rng.uniform(0.3, 0.5)))
+              for _ in range(int(rng.integers(1, 6)))]
+    n, s, d = _cl_planted(n, draws, beta, math.sqrt(2.0 * draws), sub, blocks)
+    return n, s, d, 3
+
+
+def heldout_graph(i: int, nmin: int = 200_000, nmax: int = 4_000_000):
+    """Held-out evaluation graph i: (n, src, dst, h)."""
+    return _cl_blocks_graph(splitmix64(3_000_000 + i), nmin, nmax)
+
+
+def train_large_graph(i: int, nmin: int = 100_000, nmax: int = 2_000_000):
+    """Large training graph i: (n, src, dst, h)."""
+    return _cl_blocks_graph(splitmix64(4_000_000 + i), nmin, nmax)

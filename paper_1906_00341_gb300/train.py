@@ -11,8 +11,14 @@ about 95% of the proposals fall at or below the label; Adam, batch 256.
 A proposal that overshoots only costs time: dsd_core_app_seeded tests it
 exactly and falls back to the full decomposition.
 
+The training set mixes two families of generated graphs (graphgen): small
+ones of many shapes (train_graph: ER, Chung-Lu, planted blocks; n <= 200,000)
+and large ones shaped like the evaluation workload (train_large_graph:
+Chung-Lu plus planted blocks, n 100,000 .. 2,000,000), all with seeds never
+used for evaluation.
+
 Usage (one GPU):
-    python -m paper_1906_00341_gb300.train --graphs 20000 --out proposal_h3.npz
+    python -m paper_1906_00341_gb300.train --graphs 19000 --large 1000 --out proposal_h3.npz
 
 Checkpoints are .npz files holding the flat float32 state (parameters, Adam
 moments, step) with a header: format version, parameter count, clique size,
@@ -53,9 +59,14 @@ def _gen(i):
     return gg.train_graph(i)
 
 
-def make_dataset(count, start=0, workers=8, log=print):
-    """Generate training graphs start .. start+count-1 on host processes and
-    label them on the GPU.  Returns a dict of arrays."""
+def _gen_large(i):
+    return gg.train_large_graph(i)
+
+
+def make_dataset(count, start=0, workers=8, log=print, large=False):
+    """Generate training graphs start .. start+count-1 (of the small family,
+    or with large=True of the large one) on host processes and label them
+    on the GPU.  Returns a dict of arrays."""
     X = np.zeros((count, _lib.NFEAT), np.float32)
     y = np.zeros(count, np.float32)
     mus = np.zeros(count, np.uint64)
@@ -65,10 +76,12 @@ def make_dataset(count, start=0, workers=8, log=print):
     t0 = time.time()
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        for j, (n, s, d, h) in enumerate(pool.imap(_gen, range(start, start + count), 16)):
+        gen = _gen_large if large else _gen
+        for j, (n, s, d, h) in enumerate(pool.imap(gen, range(start, start + count),
+                                                   1 if large else 16)):
             f, lab, (mu, size), m = label_graph(n, s, d, h)
             X[j], y[j], mus[j], sizes[j], ns[j], ms[j] = f, lab, mu, size, n, m
-            if log and (j + 1) % 1000 == 0:
+            if log and ((j + 1) % 1000 == 0 or (large and (j + 1) % 100 == 0)):
                 log("labelled %d/%d graphs (%.1f s)" % (j + 1, count, time.time() - t0))
     return dict(X=X, y=y, mu=mus, size=sizes, n=ns, m=ms,
                 index=np.arange(start, start + count, dtype=np.int64))
@@ -146,7 +159,10 @@ def load_checkpoint(path, stream=None):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--graphs", type=int, default=20000)
+    ap.add_argument("--graphs", type=int, default=19000, help="small training graphs")
+    ap.add_argument("--large", type=int, default=1000,
+                    help="large training graphs (the evaluation workload's shape)")
+    ap.add_argument("--large-workers", type=int, default=16)
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=256)
@@ -166,12 +182,17 @@ def main(argv=None):
             data = {k: z[k] for k in z.files}
     else:
         data = make_dataset(a.graphs, a.start, a.workers)
+        if a.large:
+            big = make_dataset(a.large, 0, a.large_workers, large=True)
+            big["index"] = -1 - big["index"]          # large graph i is stored as -1 - i
+            data = {k: np.concatenate([data[k], big[k]]) for k in data}
         if a.dataset:
             np.savez_compressed(a.dataset, **data)
     t1 = time.time()
     M, hist = train(data["X"], data["y"], a.epochs, a.batch, a.q, a.lr, a.seed)
     t2 = time.time()
-    meta = dict(graphs=int(len(data["y"])), start=int(a.start), epochs=a.epochs, batch=a.batch,
+    meta = dict(graphs=int(len(data["y"])), large=int(np.sum(data["index"] < 0)),
+                start=int(a.start), epochs=a.epochs, batch=a.batch,
                 q=a.q, lr=a.lr, seed=a.seed, label_s=round(t1 - t0, 1),
                 train_s=round(t2 - t1, 1), final=hist[-1] if hist else {})
     digest = save_checkpoint(M, a.out, 3, meta, with_optimizer=not a.no_optimizer_state)

@@ -1,4 +1,4 @@
-"""The reference arm of bench.py (the CPU oracle on a bounded sample) runs
+"""The reference arm of bench.py (the CPU oracle on the workload graph) runs
 without a GPU and prints one JSON line with the contract's keys."""
 from __future__ import annotations
 
@@ -22,4 +22,6 @@ def test_reference_arm_line():
                 "higher_is_better", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["host"]["nproc"] >= 1
+    assert line["config"]["same_config"] is True and "full workload" in line["config"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0

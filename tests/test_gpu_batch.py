@@ -91,7 +91,7 @@ def test_batch_autotune_cache(L, tmp_path):
     assert os.path.exists(cache) and open(cache).read().count("|") == 1
     b2 = L.Batch(graphs, want_cores=False, autotune_cache=cache)
     t2 = b2.info()
-    assert t1[:2] == t2[:2]
+    assert t1[:3] == t2[:3]
     # replays of the captured graph give the same answers
     b2.run()
     r1 = b2.results()
@@ -133,3 +133,55 @@ def test_batch_run_over_handles(L, orc):
     finally:
         for g in handles:
             g.close()
+
+
+def test_batch_every_tuned_shape_agrees(L, orc):
+    """Every shape of the tuner's search space (threads x CTAs per SM x lanes
+    per row scan) gives the same results, equal to the single-graph path."""
+    graphs = gg.batch(48, nmax=3000, nmedian=400.0)
+    b = L.Batch(graphs, want_cores=True)
+    ref = None
+    for threads, cps in ((256, 1), (256, 2), (512, 1), (512, 2), (1024, 1)):
+        for lanes in (32, 16, 8):
+            try:
+                b.set_shape(threads, cps, lanes)
+            except L.DSDError as e:
+                assert e.name == "DSD_ERR_UNSUPPORTED"    # does not fit on an SM
+                continue
+            assert b.info()[:3] == (threads, cps, lanes)
+            b.run()
+            res = b.results()
+            key = [(r["kmax"], r["best_k"], r["densest_mu"], r["densest_size"], r["nlevels"],
+                    r["core"].tobytes()) for r in res]
+            if ref is None:
+                ref = key
+                for (n, s, d, h), r in zip(graphs, res):
+                    want, wcore = single(L, n, s, d, h)
+                    assert r["kmax"] == want["kmax"] and np.array_equal(r["core"], wcore)
+            assert key == ref, (threads, cps, lanes)
+    assert ref is not None
+    b.close()
+
+
+def test_batch_wide_h4_graph_falls_back(L, orc):
+    """An h = 4 graph with more than 512 higher-ranked neighbours at a vertex
+    (a clique of 600) is answered inside the batch by the single-graph path;
+    the others by the batch kernel."""
+    k = 600
+    iu = np.triu_indices(k, 1)
+    wide = (k, iu[0].astype(np.uint32), iu[1].astype(np.uint32), 4)
+    graphs = gg.batch(6, nmax=2000, nmedian=300.0) + [wide]
+    b = L.Batch(graphs, want_cores=True)
+    b.run()
+    res = b.results()
+    for (n, s, d, h), r in zip(graphs, res):
+        assert r["status"] == 0
+        want, wcore = single(L, n, s, d, h)
+        assert r["kmax"] == want["kmax"] and np.array_equal(r["core"], wcore)
+    from math import comb
+    assert res[-1]["kmax"] == comb(k - 1, 3) and res[-1]["densest_mu"] == comb(k, 4)
+    b.run()
+    again = b.results()
+    for x, y in zip(again, res):
+        assert x["kmax"] == y["kmax"] and np.array_equal(x["core"], y["core"])
+    b.close()

@@ -6,11 +6,17 @@ dsd_core_app with device outputs).
   h = 3: every output against the oracle, element by element, and the
   CoreExact answer certified by one oracle cut of Algorithm 1's network on
   the oracle's own (ceil(rho'),Psi)-core (which holds every densest set).
-* R-MAT scale 22, h = 4: the oracle cannot list its 1.2e11 4-cliques in
-  test time, so the checks are sampled or structural -- the clique-degrees
-  of sampled vertices against the oracle's per-vertex count, sum(deg) =
-  h mu, core <= deg, the level records' monotonicity, and the k_max core
-  and densest level recomputed from their induced subgraphs.
+* R-MAT scale 22, h = 4 and h = 5: the oracle cannot list their 1.2e11
+  4-cliques and 7.0e12 5-cliques in test time, so the checks are sampled or
+  structural -- the clique-degrees of sampled vertices against the oracle's
+  per-vertex count, sum(deg) = h mu, core <= deg, the level records'
+  monotonicity, the k_max core and densest level recomputed from their
+  induced subgraphs, and (h = 4) one level certified by threshold pruning
+  (Def. 6): starting from all of V, vertices with fewer than k h-cliques in
+  the current induced subgraph are removed until none is left, the counts
+  taken by the library's listing on each induced subgraph, and the result
+  must be {v : core(v) >= k}; the oracle checks sampled clique-degrees of
+  that subgraph.
 """
 from __future__ import annotations
 
@@ -133,6 +139,83 @@ def test_rmat22_h4_sampled_and_structural(L, orc):
             sdeg, smu = sub.clique_degrees(h)
         assert smu == mu_want
         assert int(sdeg.min()) >= k_need
+    # a middle level certified by threshold pruning from V
+    _certify_level(L, og, h, deg, core, lk, ls, lm, 20000, rng, orc)
+
+
+def _certify_level(L, og, h, deg, core, lk, ls, lm, target, rng, orc):
+    """Threshold pruning (Def. 6) from all of V at the level whose
+    (k,Psi)-core holds about `target` vertices: vertices with fewer than k
+    h-cliques in the current induced subgraph (counted by the library's
+    listing on that subgraph) are removed until none is; the survivors must
+    be {v : core(v) >= k} with the level record's size and mu, and the
+    oracle checks sampled clique-degrees of that subgraph."""
+    jc = int(np.argmin(np.abs(ls.astype(np.int64) - target)))
+    k = int(lk[jc])
+    src, dst = og_src(og), og_dst(og)
+    sel = src < dst
+    ids = np.arange(og.n, dtype=np.int64)
+    keep = deg >= k                      # one pruning step on G itself
+    ss, dd = src[sel], dst[sel]
+    rounds = 0
+    while True:
+        rounds += 1
+        newid = np.cumsum(keep) - 1
+        e = keep[ss] & keep[dd]
+        ids, ss, dd = ids[keep], newid[ss[e]].astype(np.uint32), newid[dd[e]].astype(np.uint32)
+        with L.Graph.from_edges(ids.size, ss, dd) as sub:
+            sdeg, smu = sub.clique_degrees(h)
+        keep = sdeg >= k
+        if keep.all():
+            break
+    assert np.array_equal(ids, np.flatnonzero(core >= k))
+    assert ids.size == int(ls[jc]) and smu == int(lm[jc])
+    sog = orc.csr(ids.size, ss, dd)
+    sd = np.diff(sog.off.astype(np.int64))
+    cand = np.flatnonzero(sd <= 60)
+    if cand.size:
+        sp = rng.choice(cand, min(60, cand.size), replace=False)
+        assert np.array_equal(sdeg[sp], orc.vertex_clique_degrees(sog, h, sp))
+    return k, rounds
+
+
+def test_rmat22_h5_sampled_and_structural(L, orc):
+    h = 5
+    n, s, d, _ = gg.workload("rmat22")
+    og = orc.csr(n, s, d)
+    g, keep = _device_graph(L, n, s, d)
+    L.dsd_set_wait_limit_ms(600000)
+    try:
+        with g:
+            assert g.m == og.m
+            deg, mu = g.clique_degrees(h)
+            core, kmax = g.core_decompose(h)
+            lk, ls, lm = g.level_stats(h)
+            r = g.core_app(h)
+    finally:
+        L.dsd_set_wait_limit_ms(20000)
+    dg = np.diff(og.off.astype(np.int64))
+    rng = np.random.default_rng(55)
+    low = np.flatnonzero((dg >= 4) & (dg <= 40))
+    mid = np.flatnonzero((dg > 40) & (dg <= 120))
+    picks = np.concatenate([rng.choice(low, 150, replace=False), rng.choice(mid, 20, replace=False)])
+    assert np.array_equal(deg[picks], orc.vertex_clique_degrees(og, h, picks))
+    assert int(deg.astype(object).sum()) == h * mu
+    assert np.all(core <= deg)
+    assert kmax == int(core.max()) == r["kmax"]
+    assert np.all(np.diff(lk.astype(np.int64)) > 0) and ls[0] == n and int(lm[0]) == mu
+    assert np.all(np.diff(ls.astype(np.int64)) < 0) and np.all(np.diff(lm.astype(object)) <= 0)
+    j = int(np.flatnonzero(lk == r["best_k"])[0])
+    assert (r["densest_mu"], r["densest_size"]) == (int(lm[j]), int(ls[j]))
+    # the k_max core rebuilt as a graph of its own: every vertex in at least
+    # k_max of its h-cliques, and its mu the reported one
+    assert np.array_equal(np.flatnonzero(core >= kmax), np.sort(r["kmax_core"]))
+    mask = np.zeros(n, bool)
+    mask[r["kmax_core"]] = True
+    nn, ss, dd = _induced(og_src(og), og_dst(og), mask)
+    with L.Graph.from_edges(nn, ss, dd) as sub:
+        sdeg, smu = sub.clique_degrees(h)
+    assert smu == r["kmax_core_mu"] and int(sdeg.min()) >= kmax
 
 
 def og_src(og):
