@@ -165,8 +165,7 @@ dsd_status dsd_degeneracy_order(dsd_graph* g, uint32_t* core2, uint32_t* rank,
 /* deg[v] = deg_G(v, Psi), the number of h-clique instances containing v
  * (Def. 3), for all n vertices; *mu = mu(G, Psi) (Def. 4).  deg: n entries
  * (may be NULL to get mu only); mu may be NULL.  Both live per `mem`.
- * Errors: DSD_ERR_INVALID (h), DSD_ERR_UNSUPPORTED if h >= 4 and some
- * vertex has more than 1024 higher-ranked neighbours (degeneracy > 1024). */
+ * Errors: DSD_ERR_INVALID (h); DSD_ERR_OVERFLOW in checked mode. */
 dsd_status dsd_clique_degrees(dsd_graph* g, int h, uint64_t* deg, uint64_t* mu, int mem);
 
 /* ------------------------------------------------- core decomposition */

@@ -10,11 +10,14 @@
 // Tiers by |N+(u)|:
 //   S  <= 32   : one warp per vertex, one-word bitmap rows, lane-level DFS;
 //   M  <= 1024 : one block per vertex, 32-word bitmap rows in shared memory;
-//   L  >  1024 : h = 3 only (no bitmap needed), one block per vertex.
+//   L  >  1024 : one block per vertex; h = 3 needs no bitmap (candidates
+//                stay in global memory), h >= 4 splits the set by its next
+//                member until it fits (xl.cuh).
 // For h = 3 (r = 2) the rows are never materialised: each hit of the row
 // scan is a triangle and is counted on the spot.
 #include "cliques.cuh"
 #include "graph.cuh"
+#include "xl.cuh"
 
 namespace dsd {
 namespace {
@@ -31,7 +34,7 @@ struct CountArgs {
     unsigned long long* mu;
     uint32_t* listM;      // vertices of tier M
     uint32_t* listL;      // vertices of tier L
-    uint32_t* cntML;      // [0] tier M, [1] tier L, [2] unsupported vertices
+    uint32_t* cntML;      // [0] tier M, [1] tier L, [3] checked-mode overflow
     uint32_t* work;       // [1] dynamic queue for tier S
     uint32_t* ovf;        // checked mode: set when a counter wraps (else null)
 };
@@ -59,13 +62,9 @@ __global__ void __launch_bounds__(kCountThreads) k_count_small(CountArgs A) {
             if (d < (uint32_t)A.r) continue;            // cannot host a clique
             if (d > 32) {
                 if (lane == 0) {
-                    if (d <= kBitmapMax || A.r == 2) {
-                        int which = d <= kBitmapMax ? 0 : 1;
-                        uint32_t at = atomicAdd(&A.cntML[which], 1u);
-                        (which ? A.listL : A.listM)[at] = u;
-                    } else {
-                        atomicAdd(&A.cntML[2], 1u);     // unsupported
-                    }
+                    int which = d <= kBitmapMax ? 0 : 1;
+                    uint32_t at = atomicAdd(&A.cntML[which], 1u);
+                    (which ? A.listL : A.listM)[at] = u;
                 }
                 continue;
             }
@@ -197,6 +196,32 @@ __global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
     }
 }
 
+// Tier L for h >= 4: |N+(u)| > 1024, one block per vertex; the candidate
+// set is split by its next member until it fits the bitmap tier (xl.cuh).
+// scratch: kMaxDepth * cap entries per block.
+__global__ void __launch_bounds__(1024) k_count_xl(CountArgs A, uint32_t* scratch, uint32_t cap) {
+    extern __shared__ uint32_t smem[];
+    __shared__ unsigned long long s_root;
+    uint32_t* mine = scratch + (size_t)blockIdx.x * kMaxDepth * cap;
+    const uint32_t nL = A.cntML[1];
+    for (uint32_t it = blockIdx.x; it < nL; it += gridDim.x) {
+        const uint32_t u = A.listL[it];
+        const uint64_t b = A.split[u], e = A.off[u + 1];
+        if (threadIdx.x == 0) s_root = 0;
+        __syncthreads();
+        xl_cliques(
+            A.adj + b, (uint32_t)(e - b), A.r, A.split, A.off + 1, A.adj, mine, cap, smem,
+            [&](uint32_t x, unsigned long long c) { add_counter(&A.deg[x], c, A.ovf); },
+            [&](unsigned long long c) { s_root += c; });
+        __syncthreads();
+        if (threadIdx.x == 0 && s_root) {
+            add_counter(&A.deg[u], s_root, A.ovf);
+            add_counter(A.mu, s_root, A.ovf);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_degree_as_count(uint32_t n, const uint64_t* off, unsigned long long* deg) {
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
         deg[v] = off[v + 1] - off[v];
@@ -263,6 +288,7 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     A.deg = deg_new;
     A.mu = mu_dev;
     uint32_t* ws = nullptr;
+    uint32_t* xl_scratch = nullptr;
     DSD_TRY(dalloc(&ws, (size_t)2 * n + 8, s));
     A.listM = ws;
     A.listL = ws + n;
@@ -283,25 +309,34 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
             k_count_medium<kCountThreads><<<sms * 4, kCountThreads, smemM, s>>>(A);
         }
         note_launch();
-        if (h == 3) k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A); note_launch();
-        e = cudaGetLastError();
+        if (h == 3) {
+            k_count_large3<<<sms * 4, kCountThreads, 0, s>>>(A);
+            note_launch();
+        } else if (g->maxdplus > kBitmapMax && e == cudaSuccess) {
+            e = cudaGetLastError();
+            const uint32_t cap = g->maxdplus;
+            if (e == cudaSuccess && dalloc(&xl_scratch, (size_t)sms * kMaxDepth * cap, s) != DSD_OK)
+                e = cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) {
+                cudaFuncSetAttribute(k_count_xl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smemM);
+                k_count_xl<<<sms, 1024, smemM, s>>>(A, xl_scratch, cap);
+                note_launch();
+            }
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
-    uint32_t flags[2] = {0, 0};   // unsupported vertices, counter overflow
+    uint32_t flags[2] = {0, 0};   // (unused), counter overflow
     if (e == cudaSuccess) e = cudaMemcpyAsync(flags, A.cntML + 2, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(ws, s);
+    dev_free(xl_scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "clique count", __FILE__, __LINE__);
-    const uint32_t unsupported = flags[0];
     if (flags[1]) {
         set_error("h=%d: a clique-degree or mu exceeds 2^64 - 1 (checked mode)", h);
         return DSD_ERR_OVERFLOW;
     }
-    if (unsupported) {
-        set_error("h=%d listing needs at most %u higher-ranked neighbours per vertex; %u vertices "
-                  "exceed it (degeneracy %u)", h, kBitmapMax, unsupported, g->degeneracy);
-        return DSD_ERR_UNSUPPORTED;
-    }
-    g->prof_launches[kPhaseCount] = h == 3 ? 3 : 2;
+    g->prof_launches[kPhaseCount] = h == 3 ? 3 : (g->maxdplus > kBitmapMax ? 3 : 2);
     return st;
 }
 

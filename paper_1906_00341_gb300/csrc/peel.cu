@@ -46,6 +46,7 @@
 // rewrites a row in place (stable, so rows stay sorted) and moves wend/wnb.
 #include "cliques.cuh"
 #include "graph.cuh"
+#include "xl.cuh"
 
 #include <cooperative_groups.h>
 #include <string.h>
@@ -153,7 +154,9 @@ struct PeelParams {
     uint64_t wait_ns;
     unsigned long long mu0;
     unsigned long long k0; // initial level: kstart - 1, or 0
-    uint32_t cap;          // candidate buffer of a big item (>= max |N+|, >= 32)
+    uint32_t cap;          // candidate sets are at most this (>= max |N+|, >= 32)
+    uint32_t bcap;         // a big item's shared buffers: min(cap, kBitmapMax)
+    uint32_t* xl;          // per block (kMaxDepth + 1) * cap entries when cap > kBitmapMax
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
     uint32_t asmall;       // small-regime list capacity (0 = regime off)
@@ -499,27 +502,73 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
 }
 
 // A (v, w) item whose candidate set exceeds 32 vertices (h >= 4): one block,
-// bitmap rows of G[C] and a warp-level DFS per starting candidate.
+// bitmap rows of G[C] and a warp-level DFS per starting candidate.  When
+// N+(w) holds more than kBitmapMax entries (degeneracy above 1024) the
+// candidates are gathered into the block's global scratch; a set that still
+// exceeds kBitmapMax is split by its next member (xl.cuh).
 __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                             uint32_t* next, uint32_t* next_cnt, uint32_t* smem,
                             const uint32_t* gbm, unsigned long long& destroyed,
                             unsigned long long& bytes) {
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // cap
-    uint32_t* C = smem + 2 * P.cap;                                           // cap
-    uint32_t* rows = C + P.cap;                                               // cap * W
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);  // bcap
+    uint32_t* C = smem + 2 * P.bcap;                                          // bcap
+    uint32_t* rows = C + P.bcap;                                              // bcap * W
     __shared__ uint32_t s_nc;
     __shared__ uint32_t s_next;
     __shared__ unsigned long long s_tot;
     __shared__ uint32_t s_flag[kBitmapMax / 32], s_at[kBitmapMax / 32];
+    __shared__ uint32_t s_w[32], s_t2;
     const unsigned lane = lane_id(), nw = blockDim.x >> 5;
     uint32_t sw = st_of(P.sl[w]);
-    // candidates of v among N+(w), all warps at once: warp c tests the c-th
-    // run of 32 entries, the runs' hit masks are compacted in order
     const uint64_t b = P.wnb[w], e = P.wend[w];
-    const uint32_t runs = (uint32_t)((e - b + 31) >> 5);   // <= kBitmapMax / 32
     const uint32_t* Nv = P.wadj + P.off[v];
     const uint64_t dv = P.wend[v] - P.off[v];
     const unsigned pr = probes(dv);
+    if (e - b > kBitmapMax) {
+        // oversized N+(w): gather in order into the block's global scratch
+        uint32_t* G0 = P.xl + (size_t)blockIdx.x * (kMaxDepth + 1) * P.cap;
+        const uint32_t nc = block_filter(
+            P.wadj + b, e - b, G0,
+            [&](uint32_t x) {
+                const uint32_t st = st_of(P.sl[x]);
+                if (!(st == kAlive || (st == kFront && x > v))) return false;
+                if (gbm) return ((gbm[x >> 5] >> (x & 31)) & 1u) != 0u;
+                uint64_t pos = lower_bound_u32(Nv, dv, x);
+                return pos < dv && Nv[pos] == x;
+            },
+            s_w, &s_t2);
+        if (threadIdx.x == 0) bytes += (8ull + 4ull * pr) * (e - b) + 24;
+        if (nc > kBitmapMax) {
+            if (threadIdx.x == 0) s_tot = 0;
+            __syncthreads();
+            xl_cliques(
+                G0, nc, P.h - 2, P.wnb, P.wend, P.wadj, G0 + P.cap, P.cap, smem,
+                [&](uint32_t x, unsigned long long c) {
+                    if (st_of(P.sl[x]) == kAlive) dec_and_queue(P, x, c, k, next, next_cnt);
+                },
+                [&](unsigned long long c) { s_tot += c; });
+            __syncthreads();
+            if (threadIdx.x == 0 && s_tot) {
+                if (sw == kAlive) dec_and_queue(P, w, s_tot, k, next, next_cnt);
+                destroyed += s_tot;
+            }
+            __syncthreads();
+            return;
+        }
+        for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) C[i] = G0[i];
+        if (threadIdx.x == 0) {
+            s_nc = nc;
+            s_next = 0;
+            s_tot = 0;
+        }
+        __syncthreads();
+        if (nc < (uint32_t)(P.h - 2)) return;
+        goto bitmap;
+    }
+    {
+    // candidates of v among N+(w), all warps at once: warp c tests the c-th
+    // run of 32 entries, the runs' hit masks are compacted in order
+    const uint32_t runs = (uint32_t)((e - b + 31) >> 5);   // <= kBitmapMax / 32
     for (uint32_t c = warp_id(); c < runs; c += nw) {
         const uint64_t p = b + (uint64_t)c * 32 + lane;
         bool ok = false;
@@ -569,6 +618,8 @@ __device__ void process_big(const PeelParams& P, uint32_t v, uint32_t w, unsigne
             C[s_at[c] + __popc(bal & ((1u << lane) - 1u))] = P.wadj[b + (uint64_t)c * 32 + lane];
     }
     __syncthreads();
+    }
+bitmap:
     uint32_t nc = s_nc;
     uint32_t W = (nc + 31) >> 5;
     for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
@@ -1504,12 +1555,8 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.k0 = kstart ? kstart - 1 : 0;
     P.snap = snap;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
+    P.bcap = P.cap < kBitmapMax ? P.cap : kBitmapMax;
     P.compact = h >= 3 ? 1 : 0;
-    if (h >= 4 && maxdplus > kBitmapMax) {
-        set_error("h=%d peeling needs at most %u higher-ranked neighbours per vertex "
-                  "(max here %u)", h, kBitmapMax, maxdplus);
-        return DSD_ERR_UNSUPPORTED;
-    }
     // Big items (candidate sets above kWarpCand vertices, one block each)
     // for h >= 4; every candidate set fits 32-word rows.
     const bool big_items = h >= 4;
@@ -1532,8 +1579,10 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
         P.hub_min = 4 * P.heavy_min;
     }
     if (big_items) {
-        size_t W = (P.cap + 31) / 32;
-        size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
+        size_t W = (P.bcap + 31) / 32;
+        size_t big = (size_t)3 * P.bcap + (size_t)P.bcap * W;
+        // the split search of oversized sets uses the full bitmap tier layout
+        if (P.cap > kBitmapMax) big = (size_t)3 * kBitmapMax + (size_t)kBitmapMax * 32;
         if (big > work) work = big;
     }
     size_t room = budget > work * 4 + 12 * 1024 ? budget - work * 4 - 12 * 1024 : 0;
@@ -1570,6 +1619,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     uint32_t* rows_g = nullptr;
     uint2* big = nullptr;
     uint32_t* heavy = nullptr;
+    uint32_t* xl = nullptr;
     uint32_t* hub_bm = nullptr;
     uint32_t* hubs = nullptr;
     ulonglong2* jblk = nullptr;
@@ -1593,6 +1643,10 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     }
     if (P.heavy_min && (st = dalloc(&heavy, n, s)) != DSD_OK) goto done;
     P.heavy = heavy;
+    if (big_items && P.cap > kBitmapMax &&
+        (st = dalloc(&xl, (size_t)sms * (kMaxDepth + 1) * P.cap, s)) != DSD_OK)
+        goto done;
+    P.xl = xl;
     if (P.hub_slots) {
         if ((st = dalloc(&hub_bm, (size_t)2 * P.hub_slots * P.hub_words, s)) != DSD_OK) goto done;
         if ((st = dalloc(&hubs, (size_t)2 * P.hub_slots, s)) != DSD_OK) goto done;
@@ -1703,6 +1757,7 @@ done:
     dev_free(rows_g, s);
     dev_free(big, s);
     dev_free(heavy, s);
+    dev_free(xl, s);
     dev_free(hub_bm, s);
     dev_free(hubs, s);
     dev_free(jblk, s);

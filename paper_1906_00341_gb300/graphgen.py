@@ -207,7 +207,8 @@ def random_small(n: int, p: float, seed: int, loops: bool = True,
 #                max expected degree sqrt(sum w), seed 7; plus five planted
 #                G(300, 0.4) blocks on disjoint random vertices     (h = 3)
 # Scaled-down variants (same recipe, smaller n) serve the parity tests that
-# the oracle finishes in seconds.
+# the oracle finishes in seconds (cl50k, rmat14) and kernel profiles whose
+# inputs still exceed the 129 MB L2 (rmat21: 2^21 vertices, 2^25 draws).
 # ---------------------------------------------------------------------------
 
 def _cl_planted(n, draws, beta, wmax, seed, blocks, wsum=None):
@@ -237,6 +238,9 @@ def workload(name: str):
     if name == "rmat14":
         n, s, d = rmat(14, 16, 0.57, 0.19, 0.19, 0)
         return n, s, d, [4, 5]
+    if name == "rmat21":
+        n, s, d = rmat(21, 16, 0.57, 0.19, 0.19, 0)
+        return n, s, d, [4, 5]
     if name == "cl4m":
         draws = 64_000_000
         n, s, d = _cl_planted(4_000_000, draws, 2.2,
@@ -245,7 +249,7 @@ def workload(name: str):
     raise KeyError(name)
 
 
-WORKLOADS = ("er2000", "cl1m", "cl50k", "rmat22", "rmat14", "cl4m")
+WORKLOADS = ("er2000", "cl1m", "cl50k", "rmat22", "rmat14", "rmat21", "cl4m")
 
 
 # ---------------------------------------------------------------------------
