@@ -34,51 +34,42 @@ constexpr int kScanChunks = 4;
 
 // Hits of the list adj[b, e) (ascending) in the sorted candidates C[0, nc)
 // whose largest entry is cmax, by one warp: cnt[pos] += 1 for each hit
-// (shared counters); returns this lane's number of hits.  The 16-byte
-// aligned body of the list is read with 128-bit loads (four ids per lane,
-// 128 per warp-wide load), the unaligned head and tail (three ids at most
-// each) with 32-bit loads; the scan stops after the first step that passes
-// cmax.  adj must be 16-byte aligned.  *read_end (if given) receives the end
-// of what was read.
+// (shared counters); returns this lane's number of hits.  Each step loads
+// kScanChunks coalesced 32-entry chunks at once, lane l taking entry l of
+// each, so that the lanes' binary searches look for neighbouring ids and
+// follow nearly the same path through C; the scan stops after the first step
+// that passes cmax.  *read_end (if given) receives the end of what was read.
 template <class T>
 __device__ __forceinline__ unsigned scan_row_hits(const uint32_t* C, uint32_t nc, uint32_t cmax,
                                                   const uint32_t* adj, uint64_t b, uint64_t e,
                                                   T* cnt, uint64_t* read_end = nullptr) {
     const unsigned lane = lane_id();
     unsigned hits = 0;
-    auto test = [&](uint32_t y) {
-        if (y <= cmax) {
-            uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
-            if (pos < nc && C[pos] == y) {
-                atomicAdd(&cnt[pos], (T)1);
-                hits++;
+    uint64_t p0 = b;
+    for (; p0 < e; p0 += 32 * kScanChunks) {
+        uint32_t ys[kScanChunks];
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            ys[u] = p < e ? adj[p] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            const uint32_t y = ys[u];
+            if (y <= cmax) {
+                uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
+                if (pos < nc && C[pos] == y) {
+                    atomicAdd(&cnt[pos], (T)1);
+                    hits++;
+                }
             }
         }
-    };
-    uint64_t a = (b + 3) & ~(uint64_t)3;        // first 16-byte boundary
-    if (a > e) a = e;
-    const uint64_t be = a + ((e - a) & ~(uint64_t)3);   // end of the aligned body
-    if (b + lane < a) test(adj[b + lane]);
-    uint64_t p0 = a;
-    bool past = false;
-    for (; p0 < be; p0 += 128) {
-        const uint64_t q = p0 + 4 * (uint64_t)lane;
-        uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-        if (q < be) v = *reinterpret_cast<const uint4*>(adj + q);
-        test(v.x);
-        test(v.y);
-        test(v.z);
-        test(v.w);
-        // stop once a loaded id passes cmax (lane 31's last one, if it is
-        // inside the body; otherwise the body ends with this step)
-        if (p0 + 124 < be && __shfl_sync(0xffffffffu, v.w, 31) > cmax) {
-            p0 += 128;
-            past = true;
+        if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) {
+            p0 += 32 * kScanChunks;
             break;
         }
     }
-    if (!past && be + lane < e) test(adj[be + lane]);
-    if (read_end) *read_end = past ? (p0 < e ? p0 : e) : e;
+    if (read_end) *read_end = p0 < e ? p0 : e;
     return hits;
 }
 

@@ -943,30 +943,36 @@ constexpr unsigned kSmallGrid = 152 * 8;   // blocks of 256 threads (warp per no
 constexpr unsigned kBigGrid = 152 * 4;     // blocks of kBigThreads (block per node)
 
 // Backward breadth-first search from t: exact residual distances to t, N for
-// nodes that cannot reach it (and for s); resets the current arcs.
+// nodes that cannot reach it (and for s); resets the current arcs.  The
+// levels are queued kBfsBatch at a time and the host reads the frontier size
+// once per batch: a level whose input frontier is empty does nothing.
+constexpr uint32_t kBfsBatch = 8;
+
 dsd_status global_relabel(const PR& P, CutWork& w, cudaStream_t s) {
     uint32_t *fs = w.f[0], *fb = w.f[1], *os = w.f[2], *ob = w.f[3];
     uint32_t* cin = w.ctr + 2;
     uint32_t* cout = w.ctr + 4;
     k_bfs_init<<<grid_for_n(P.N), 256, 0, s>>>(P, fs, fb, cin); note_launch();
-    for (uint32_t d = 0;; d++) {
-        uint32_t nc[2] = {0, 0};
-        DSD_CU(cudaMemsetAsync(cout, 0, 8, s));
-        k_bfs_small<<<kSmallGrid, 256, 0, s>>>(P, fs, cin, d, os, ob, cout);
-        k_bfs_big<<<kBigGrid, kBigThreads, 0, s>>>(P, fb, cin, d, os, ob, cout);
-        note_launch();
-        note_launch();
-        DSD_CU(cudaMemcpyAsync(nc, cout, 8, cudaMemcpyDeviceToHost, s));
+    for (uint32_t d0 = 0;; d0 += kBfsBatch) {
+        for (uint32_t d = d0; d < d0 + kBfsBatch; d++) {
+            DSD_CU(cudaMemsetAsync(cout, 0, 8, s));
+            k_bfs_small<<<kSmallGrid, 256, 0, s>>>(P, fs, cin, d, os, ob, cout);
+            k_bfs_big<<<kBigGrid, kBigThreads, 0, s>>>(P, fb, cin, d, os, ob, cout);
+            note_launch();
+            note_launch();
+            uint32_t* t;
+            t = fs; fs = os; os = t;
+            t = fb; fb = ob; ob = t;
+            t = cin; cin = cout; cout = t;
+        }
+        uint32_t nc[2] = {0, 0};   // the last level's output frontier (now cin)
+        DSD_CU(cudaMemcpyAsync(nc, cin, 8, cudaMemcpyDeviceToHost, s));
         DSD_CU(cudaStreamSynchronize(s));
         if (nc[0] + nc[1] == 0) break;
-        if (d > P.N) {
+        if (d0 > P.N) {
             set_error("breadth-first search did not settle");
             return DSD_ERR_INTERNAL;
         }
-        uint32_t* t;
-        t = fs; fs = os; os = t;
-        t = fb; fb = ob; ob = t;
-        t = cin; cin = cout; cout = t;
     }
     k_bfs_finish<<<grid_for_n(P.N), 256, 0, s>>>(P); note_launch();
     DSD_LAUNCHED();
