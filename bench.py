@@ -755,7 +755,7 @@ def run_c3(args, local):
         L.dsd_clique_degrees(g, h, 0, mu.ctypes.data, L.DSD_MEM_HOST)
         mu = int(mu[0])
         n_, m_und = L.dsd_graph_info(g)
-        roof = listing_roofline(L, g, float(ms[3]), peak, peak_kind, "count_rmat22")
+        roof = listing_roofline(L, g, float(ms[3]), peak, peak_kind, "count_rmat22_h%d" % h)
         L.dsd_graph_destroy(g)
         times = []
         for _ in range(max(args.c3_steps, 1)):
