@@ -16,7 +16,9 @@
 // jump), the levels are independent processes.
 //
 // One block per level (the largest levels first).  Per step the block
-//   - takes the alive member of L_k of least (count, caller id),
+//   - takes the alive member of L_k of least (count, caller id): from a
+//     bucket queue when the level has one (below), else by a scan of the
+//     level,
 //   - compares the density of the current set with the level's best,
 //   - removes it and lowers the count of every alive member of L_k that
 //     shares an h-clique with it inside the current set.  The cliques through
@@ -26,6 +28,20 @@
 // Level 0 (vertices in no h-clique) is removed in id order with no change.
 // A final pass takes, over the levels in order, the earliest set of
 // greatest density and emits it in caller ids.
+//
+// Bucket queue of a level: for every count c < B (B <= k + 1), a bitmap over
+// the level's positions with bit i set iff member i is alive with count c,
+// two summary levels above it (bit t of a summary word: word t below may be
+// non-empty), the population of every bucket and a bitmap of the buckets
+// that may be non-empty.  The least (count, position) is the first set bit
+// of the first non-empty bucket; with B = k + 1 that bucket always exists,
+// since the minimum stays at or below k.  A count lowered from d to d - c
+// toggles (XOR) its bit in buckets d and d - c: toggles commute, so the
+// lowerings of one step may run in any order and the buckets are exact once
+// they are all done; summaries are only ever set by the lowerings and are
+// cleared lazily by the search.  Members of count 0 lie in no h-clique of
+// the current set, so their removal changes no count: they leave one after
+// another in position order without the clique listing.
 #include "cliques.cuh"
 #include "graph.cuh"
 
@@ -62,6 +78,44 @@ struct AppParams {
     uint32_t* bigw;           // per block: bigcap entries
     uint32_t bigcap;
     uint32_t cap;             // big candidate sets: >= max |N+|, >= 32
+    uint32_t qwords;          // shared words of the bucket queue (after the scratch)
+    uint32_t scratch_words;   // shared words of the warp and big-set scratch
+    const uint32_t* qB;       // per level: buckets B (0 = no queue: the scan)
+    const uint64_t* qoff;     // per level: word offset in qg, or kQShared
+    uint32_t* qg;             // bucket queues of levels too large for shared memory
+    uint32_t* err;            // [1] set when the queue and the counts disagree
+};
+
+constexpr uint64_t kQShared = ~0ull;
+constexpr uint32_t kQMaxBuckets = 1024;   // the bucket bitmap is one warp's 32 words
+
+__host__ __device__ inline uint32_t q_words_per_bucket(uint32_t sz) {
+    uint32_t n1 = (sz + 31) / 32, n2 = (n1 + 31) / 32, n3 = (n2 + 31) / 32;
+    return n1 + n2 + n3;
+}
+__host__ __device__ inline uint64_t q_words(uint32_t sz, uint32_t B) {
+    return (uint64_t)B * q_words_per_bucket(sz) + B + 32;
+}
+
+// One level's bucket queue (a view; B = 0: none).
+struct AppQ {
+    uint32_t *M, *S, *T;      // bitmaps and summaries, bucket-major
+    uint32_t *pop, *bsum;
+    uint32_t B, n1, n2, n3, base;
+
+    __device__ void toggle(unsigned long long d, uint32_t i) const {
+        if (d >= B) return;
+        const uint32_t c = (uint32_t)d, bit = 1u << (i & 31u);
+        const uint32_t old = atomicXor(&M[(size_t)c * n1 + (i >> 5)], bit);
+        if (old & bit) {
+            atomicSub(&pop[c], 1u);
+        } else {
+            atomicAdd(&pop[c], 1u);
+            atomicOr(&S[(size_t)c * n2 + (i >> 10)], 1u << ((i >> 5) & 31u));
+            atomicOr(&T[(size_t)c * n3 + (i >> 15)], 1u << ((i >> 10) & 31u));
+            atomicOr(&bsum[c >> 5], 1u << (c & 31u));
+        }
+    }
 };
 
 __device__ __forceinline__ bool ratio_gt(unsigned long long a, unsigned long long b,
@@ -79,11 +133,17 @@ __device__ __forceinline__ bool in_set(const AppParams& P, uint32_t x, unsigned 
     return c > k || (c == k && P.step[P.posof[x]] == kNoStep);
 }
 
-__device__ __forceinline__ void lower(const AppParams& P, uint32_t x, unsigned long long k,
-                                      unsigned long long c) {
+__device__ __forceinline__ void lower(const AppParams& P, const AppQ& Q, uint32_t x,
+                                      unsigned long long k, unsigned long long c) {
     if (c && P.core[x] == k) {
         uint32_t p = P.posof[x];
-        if (P.step[p] == kNoStep) atomicAdd(&P.deg[p], 0ull - c);
+        if (P.step[p] == kNoStep) {
+            unsigned long long old = atomicAdd(&P.deg[p], 0ull - c);
+            if (Q.B) {
+                Q.toggle(old, p - Q.base);
+                Q.toggle(old - c, p - Q.base);
+            }
+        }
     }
 }
 
@@ -92,8 +152,9 @@ __device__ __forceinline__ void lower(const AppParams& P, uint32_t x, unsigned l
 // and an alive level member loses it on the spot; else the first `keep` go
 // to C, and with keep = kAppWarpCand the walk stops once there are more.
 template <bool DIRECT>
-__device__ __forceinline__ uint32_t app_gather(const AppParams& P, uint32_t v, uint32_t w,
-                                               unsigned long long k, uint32_t* C, uint32_t keep) {
+__device__ __forceinline__ uint32_t app_gather(const AppParams& P, const AppQ& Q, uint32_t v,
+                                               uint32_t w, unsigned long long k, uint32_t* C,
+                                               uint32_t keep) {
     const unsigned lane = lane_id();
     const uint32_t* Nv = P.adj + P.off[v];
     const uint64_t dv = P.off[v + 1] - P.off[v];
@@ -112,7 +173,7 @@ __device__ __forceinline__ uint32_t app_gather(const AppParams& P, uint32_t v, u
         }
         unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (DIRECT) {
-            if (ok) lower(P, x, k, 1ull);
+            if (ok) lower(P, Q, x, k, 1ull);
         } else {
             uint32_t at = nc + __popc(bal & ((1u << lane) - 1u));
             if (ok && at < keep) C[at] = x;
@@ -127,16 +188,16 @@ __device__ __forceinline__ uint32_t app_gather(const AppParams& P, uint32_t v, u
 // w, counted by one warp when their candidate set fits kAppWarpCand; their
 // alive level members lose them.  Returns false when the set is larger
 // (h >= 4; the block takes it afterwards).
-__device__ bool app_item(const AppParams& P, uint32_t v, uint32_t w, unsigned long long k,
-                         uint32_t* C, unsigned* cnt, uint32_t* rows) {
+__device__ bool app_item(const AppParams& P, const AppQ& Q, uint32_t v, uint32_t w,
+                         unsigned long long k, uint32_t* C, unsigned* cnt, uint32_t* rows) {
     const unsigned lane = lane_id();
     const int r = P.h - 2;
     if (r == 1) {
-        uint32_t nc = app_gather<true>(P, v, w, k, C, 0);
-        if (lane == 0) lower(P, w, k, nc);
+        uint32_t nc = app_gather<true>(P, Q, v, w, k, C, 0);
+        if (lane == 0) lower(P, Q, w, k, nc);
         return true;
     }
-    uint32_t nc = app_gather<false>(P, v, w, k, C, kAppWarpCand);
+    uint32_t nc = app_gather<false>(P, Q, v, w, k, C, kAppWarpCand);
     __syncwarp();
     if (nc < (uint32_t)r) return true;
     if (nc > kAppWarpCand) return false;
@@ -158,24 +219,24 @@ __device__ bool app_item(const AppParams& P, uint32_t v, uint32_t w, unsigned lo
             tot = warp_dfs32(rows, nc, r, cnt);
         }
         __syncwarp();
-        for (uint32_t i = lane; i < nc; i += 32) lower(P, C[i], k, cnt[i]);
+        for (uint32_t i = lane; i < nc; i += 32) lower(P, Q, C[i], k, cnt[i]);
         __syncwarp();
     }
-    if (lane == 0) lower(P, w, k, tot);
+    if (lane == 0) lower(P, Q, w, k, tot);
     return true;
 }
 
 // A candidate set above kAppWarpCand vertices (h >= 4): the whole block,
 // bitmap rows of G[C] and the block DFS.
-__device__ void app_big(const AppParams& P, uint32_t v, uint32_t w, unsigned long long k,
-                        uint32_t* smem) {
+__device__ void app_big(const AppParams& P, const AppQ& Q, uint32_t v, uint32_t w,
+                        unsigned long long k, uint32_t* smem) {
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);   // cap
     uint32_t* C = smem + 2 * P.cap;                                            // cap
     uint32_t* rows = C + P.cap;                                                // cap * W
     __shared__ uint32_t s_nc, s_next;
     __shared__ unsigned long long s_tot;
     if (warp_id() == 0) {
-        uint32_t nc = app_gather<false>(P, v, w, k, C, P.cap);
+        uint32_t nc = app_gather<false>(P, Q, v, w, k, C, P.cap);
         if (lane_id() == 0) {
             s_nc = nc;
             s_next = 0;
@@ -192,10 +253,70 @@ __device__ void app_big(const AppParams& P, uint32_t v, uint32_t w, unsigned lon
     unsigned long long mine = block_dfs(rows, nc, W, P.h - 2, cnt, &s_next);
     if (mine) atomicAdd(&s_tot, mine);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) lower(P, C[i], k, cnt[i]);
-    if (threadIdx.x == 0) lower(P, w, k, s_tot);
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) lower(P, Q, C[i], k, cnt[i]);
+    if (threadIdx.x == 0) lower(P, Q, w, k, s_tot);
     __syncthreads();
 }
+
+// Warp search of a level's queue (one warp, nothing else touching the
+// queue): the least bucket with members, B if none; stale bucket bits are
+// cleared on the way.  Values read by lane 0 are broadcast, so every lane
+// takes the same branch.
+__device__ __forceinline__ uint32_t q_least_bucket(const AppQ& Q) {
+    const unsigned lane = lane_id();
+    volatile uint32_t* bs = Q.bsum;
+    volatile uint32_t* pop = Q.pop;
+    const uint32_t nbw = (Q.B + 31) / 32;
+    for (;;) {
+        uint32_t w = lane < nbw ? bs[lane] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, w != 0);
+        if (!bal) return Q.B;
+        const uint32_t t = __ffs(bal) - 1;
+        w = __shfl_sync(0xffffffffu, w, t);
+        const uint32_t b = t * 32 + __ffs(w) - 1;
+        uint32_t pb = lane == 0 ? pop[b] : 0u;
+        pb = __shfl_sync(0xffffffffu, pb, 0);
+        if (pb) return b;
+        if (lane == 0) bs[t] = w & ~(1u << (b & 31u));
+        __syncwarp();
+    }
+}
+
+// The first position in bucket b (~0u if the summaries lead to none); stale
+// summary bits are cleared on the way.
+__device__ __forceinline__ uint32_t q_first(const AppQ& Q, uint32_t b) {
+    const unsigned lane = lane_id();
+    volatile uint32_t* T = Q.T + (size_t)b * Q.n3;
+    volatile uint32_t* S = Q.S + (size_t)b * Q.n2;
+    volatile uint32_t* M = Q.M + (size_t)b * Q.n1;
+    for (;;) {
+        uint32_t tw = lane < Q.n3 ? T[lane] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, tw != 0);
+        if (!bal) return ~0u;
+        const uint32_t t = __ffs(bal) - 1;
+        tw = __shfl_sync(0xffffffffu, tw, t);
+        const uint32_t si = t * 32 + __ffs(tw) - 1;
+        uint32_t sw = lane == 0 ? S[si] : 0u;
+        sw = __shfl_sync(0xffffffffu, sw, 0);
+        if (!sw) {
+            if (lane == 0) T[t] = tw & ~(1u << (si & 31u));
+            __syncwarp();
+            continue;
+        }
+        const uint32_t mi = si * 32 + __ffs(sw) - 1;
+        uint32_t mw = lane == 0 ? M[mi] : 0u;
+        mw = __shfl_sync(0xffffffffu, mw, 0);
+        if (!mw) {
+            if (lane == 0) S[si] = sw & ~(1u << (mi & 31u));
+            __syncwarp();
+            continue;
+        }
+        return mi * 32 + __ffs(mw) - 1;
+    }
+}
+
+constexpr uint32_t kPickScan = 0xffffffffu;   // no queue pick: scan the level
+constexpr uint32_t kPickDone = 0xfffffffeu;   // every member removed
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_peel_app(AppParams P) {
@@ -203,7 +324,7 @@ __global__ void __launch_bounds__(NT) k_peel_app(AppParams P) {
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_kd[NW];
     __shared__ uint32_t s_kp[NW];
-    __shared__ uint32_t s_lv, s_pick, s_nbig;
+    __shared__ uint32_t s_lv, s_pick, s_nbig, s_it;
     const unsigned lane = lane_id(), wid = warp_id();
     uint32_t* wC = smem + (size_t)wid * 3 * kAppWarpCand;
     unsigned* wCnt = wC + kAppWarpCand;
@@ -233,68 +354,143 @@ __global__ void __launch_bounds__(NT) k_peel_app(AppParams P) {
             }
             continue;
         }
+        // the level's bucket queue, if it has one
+        AppQ Q;
+        Q.B = P.qB[j];
+        Q.n1 = (sz + 31) / 32;
+        Q.n2 = (Q.n1 + 31) / 32;
+        Q.n3 = (Q.n2 + 31) / 32;
+        Q.base = base;
+        Q.M = Q.S = Q.T = Q.pop = Q.bsum = nullptr;
+        if (Q.B) {
+            uint32_t* R = P.qoff[j] == kQShared ? smem + P.scratch_words : P.qg + P.qoff[j];
+            Q.M = R;
+            Q.S = Q.M + (size_t)Q.B * Q.n1;
+            Q.T = Q.S + (size_t)Q.B * Q.n2;
+            Q.pop = Q.T + (size_t)Q.B * Q.n3;
+            Q.bsum = Q.pop + Q.B;
+            const uint64_t nw = q_words(sz, Q.B);
+            for (uint64_t i = threadIdx.x; i < nw; i += NT) R[i] = 0;
+            __syncthreads();
+        }
         for (uint32_t i = threadIdx.x; i < sz; i += NT) {
-            P.deg[base + i] = P.snap[P.rank_at[base + i]];
+            const unsigned long long d = P.snap[P.rank_at[base + i]];
+            P.deg[base + i] = d;
             P.step[base + i] = kNoStep;
+            Q.toggle(d, i);
         }
         unsigned long long bmu = mu;
-        uint32_t bsize = size0, bstep = 0;
+        uint32_t bsize = size0, bstep = 0, it = 0;   // thread 0's (it: warp 0's)
         __syncthreads();
-        for (uint32_t it = 0; it < sz; it++) {
-            // least (count, position); positions ascend with the caller id
-            unsigned long long md = ~0ull;
-            uint32_t mp = 0xffffffffu;
-            for (uint32_t i = threadIdx.x; i < sz; i += NT) {
-                if (P.step[base + i] != kNoStep) continue;
-                unsigned long long d = P.deg[base + i];
-                if (d < md) { md = d; mp = i; }   // i ascends: ties keep the first
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long od = __shfl_xor_sync(0xffffffffu, md, o);
-                uint32_t op = __shfl_xor_sync(0xffffffffu, mp, o);
-                if (od < md || (od == md && op < mp)) { md = od; mp = op; }
-            }
-            if (lane == 0) { s_kd[wid] = md; s_kp[wid] = mp; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned long long bd = s_kd[0];
-                uint32_t bp = s_kp[0];
-                for (int w2 = 1; w2 < NW; w2++)
-                    if (s_kd[w2] < bd || (s_kd[w2] == bd && s_kp[w2] < bp)) {
-                        bd = s_kd[w2];
-                        bp = s_kp[w2];
+        for (;;) {
+            // ---- the next removal: the queue's least (count, position), the
+            // members of count 0 leaving at once; or a scan of the level
+            if (wid == 0) {
+                uint32_t pick = kPickScan;
+                while (Q.B) {
+                    const uint32_t b = q_least_bucket(Q);
+                    if (b == Q.B) break;   // only counts >= B left (B < k + 1)
+                    const uint32_t i = q_first(Q, b);
+                    if (i == ~0u) {
+                        if (lane == 0) atomicOr(P.err, 1u);
+                        pick = kPickDone;
+                        break;
                     }
-                // the set before this removal: size0 - it vertices, mu cliques
-                if (it > 0 && ratio_gt(mu, size0 - it, bmu, bsize)) {
-                    bmu = mu;
-                    bsize = size0 - it;
-                    bstep = it;
+                    if (lane == 0) {
+                        Q.M[(size_t)b * Q.n1 + (i >> 5)] &= ~(1u << (i & 31u));
+                        Q.pop[b] -= 1u;
+                        if (P.deg[base + i] != b) atomicOr(P.err, 2u);
+                        // the set before this removal: size0 - it vertices, mu cliques
+                        if (it > 0 && ratio_gt(mu, size0 - it, bmu, bsize)) {
+                            bmu = mu;
+                            bsize = size0 - it;
+                            bstep = it;
+                        }
+                        mu -= b;
+                        P.step[base + i] = it;
+                    }
+                    it++;
+                    __syncwarp();
+                    if (b != 0) {
+                        pick = i;
+                        break;
+                    }
+                    if (it == sz) {
+                        pick = kPickDone;
+                        break;
+                    }
                 }
-                mu -= bd;
-                P.step[base + bp] = it;
-                s_pick = bp;
-                s_nbig = 0;
+                if (lane == 0) {
+                    s_pick = pick;
+                    s_it = it;
+                    s_nbig = 0;
+                }
             }
             __syncthreads();
-            const uint32_t v = P.rank_at[base + s_pick];
+            uint32_t pick = s_pick;
+            if (pick == kPickDone) break;
+            if (pick == kPickScan) {
+                // least (count, position); positions ascend with the caller id
+                unsigned long long md = ~0ull;
+                uint32_t mp = 0xffffffffu;
+                for (uint32_t i = threadIdx.x; i < sz; i += NT) {
+                    if (P.step[base + i] != kNoStep) continue;
+                    unsigned long long d = P.deg[base + i];
+                    if (d < md) { md = d; mp = i; }   // i ascends: ties keep the first
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long od = __shfl_xor_sync(0xffffffffu, md, o);
+                    uint32_t op = __shfl_xor_sync(0xffffffffu, mp, o);
+                    if (od < md || (od == md && op < mp)) { md = od; mp = op; }
+                }
+                if (lane == 0) { s_kd[wid] = md; s_kp[wid] = mp; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned long long bd = s_kd[0];
+                    uint32_t bp = s_kp[0];
+                    for (int w2 = 1; w2 < NW; w2++)
+                        if (s_kd[w2] < bd || (s_kd[w2] == bd && s_kp[w2] < bp)) {
+                            bd = s_kd[w2];
+                            bp = s_kp[w2];
+                        }
+                    if (bd < Q.B) atomicOr(P.err, 4u);   // the queue holds every count < B
+                    if (it > 0 && ratio_gt(mu, size0 - it, bmu, bsize)) {
+                        bmu = mu;
+                        bsize = size0 - it;
+                        bstep = it;
+                    }
+                    mu -= bd;
+                    P.step[base + bp] = it;
+                    s_pick = bp;
+                    s_it = it + 1;
+                }
+                if (wid == 0) it++;
+                __syncthreads();
+                pick = s_pick;
+            }
+            // ---- the cliques through the removed vertex lower its partners
+            const uint32_t v = P.rank_at[base + pick];
             const uint64_t vb = P.off[v], ve = P.off[v + 1];
             if (P.h == 2) {
-                for (uint64_t p = vb + threadIdx.x; p < ve; p += NT) lower(P, P.adj[p], k, 1ull);
+                for (uint64_t p = vb + threadIdx.x; p < ve; p += NT)
+                    lower(P, Q, P.adj[p], k, 1ull);
             } else {
                 for (uint64_t p = vb + wid; p < ve; p += NW) {
                     uint32_t w = P.adj[p];
                     if (!in_set(P, w, k)) continue;
-                    if (!app_item(P, v, w, k, wC, wCnt, wRows) && lane == 0) {
+                    if (!app_item(P, Q, v, w, k, wC, wCnt, wRows) && lane == 0) {
                         uint32_t at = atomicAdd(&s_nbig, 1u);
                         if (at < P.bigcap) bigw[at] = w;
                     }
                 }
                 __syncthreads();
                 const uint32_t nb = s_nbig;
-                for (uint32_t b = 0; b < nb && b < P.bigcap; b++) app_big(P, v, bigw[b], k, smem);
+                for (uint32_t b = 0; b < nb && b < P.bigcap; b++)
+                    app_big(P, Q, v, bigw[b], k, smem);
             }
             __syncthreads();
+            if (s_it >= sz) break;
         }
         if (threadIdx.x == 0)
             P.best[j] = make_ulonglong2(bmu, ((unsigned long long)bsize << 32) | bstep);
@@ -440,7 +636,11 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
     cudaError_t e = cudaSuccess;
     PeelResult pr;
     uint32_t nl = 0;
-    std::vector<uint32_t> hls;
+    std::vector<uint32_t> hls, hqB;
+    std::vector<uint64_t> hk, hqoff;
+    uint32_t *qBv = nullptr, *qg = nullptr;
+    uint64_t* qoffv = nullptr;
+    uint32_t herr = 0;
 #define APP_TRY(x)                                \
     do {                                          \
         st = (x);                                 \
@@ -483,7 +683,9 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
     k_app_place<<<app_grid(n), 256, 0, s>>>(n, lev, ls, nl, g->old_of, cur, ids); note_launch();
     APP_CU(cudaGetLastError());
     hls.resize(nl);
+    hk.resize(nl);
     APP_CU(cudaMemcpyAsync(hls.data(), ls, (size_t)nl * 4, cudaMemcpyDeviceToHost, s));
+    APP_CU(cudaMemcpyAsync(hk.data(), lk, (size_t)nl * 8, cudaMemcpyDeviceToHost, s));
     APP_CU(cudaStreamSynchronize(s));
     {
         std::vector<uint32_t> len(nl), order(nl);
@@ -538,7 +740,43 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
             size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
             if (big > words) words = big;
         }
-        size_t smem = words * 4;
+        // bucket queues: in shared memory after the scratch where they fit
+        // (every count 0..k), else in global memory within a budget, else
+        // the buckets that fit shared memory with the scan behind them
+        const size_t qsh = std::min<size_t>(12288, 220 * 1024 / 4 > words ? 220 * 1024 / 4 - words : 0);
+        P.scratch_words = (uint32_t)words;
+        P.qwords = (uint32_t)qsh;
+        hqB.assign(nl, 0u);
+        hqoff.assign(nl, kQShared);
+        uint64_t gwords = 0;
+        const uint64_t gbudget = (uint64_t)64 << 20;   // words (256 MB)
+        for (uint32_t j = 0; j < nl; j++) {
+            const uint32_t sz = hls[j] - (j + 1 < nl ? hls[j + 1] : 0u);
+            if (hk[j] == 0 || sz == 0 || sz > (1u << 20)) continue;   // the warp search: <= 32^4
+            const uint32_t bf = hk[j] + 1 < kQMaxBuckets ? (uint32_t)hk[j] + 1 : kQMaxBuckets;
+            const uint64_t need = q_words(sz, bf);
+            if (need <= qsh) {
+                hqB[j] = bf;
+            } else if (gwords + need <= gbudget) {
+                hqB[j] = bf;
+                hqoff[j] = gwords;
+                gwords += need;
+            } else {
+                const uint64_t wpb = q_words_per_bucket(sz) + 1;
+                const uint64_t b = qsh > 32 ? (qsh - 32) / wpb : 0;
+                hqB[j] = (uint32_t)(b < bf ? b : bf);
+            }
+        }
+        APP_TRY(dalloc(&qBv, (size_t)nl, s));
+        APP_TRY(dalloc(&qoffv, (size_t)nl, s));
+        APP_TRY(dalloc(&qg, (size_t)gwords + 1, s));
+        APP_CU(cudaMemcpyAsync(qBv, hqB.data(), (size_t)nl * 4, cudaMemcpyHostToDevice, s));
+        APP_CU(cudaMemcpyAsync(qoffv, hqoff.data(), (size_t)nl * 8, cudaMemcpyHostToDevice, s));
+        P.qB = qBv;
+        P.qoff = qoffv;
+        P.qg = qg;
+        P.err = stepv + n + 1;
+        size_t smem = (words + qsh) * 4;
         const void* fn = (const void*)k_peel_app<kAppNT>;
         if (smem > 48 * 1024)
             APP_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -565,9 +803,16 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
         P.bigcap = (uint32_t)(maxrow + 1);
         APP_TRY(dalloc(&bigw, (size_t)grid * P.bigcap + 1, s));
         P.bigw = bigw;
-        APP_CU(cudaMemsetAsync(P.queue, 0, 4, s));
+        APP_CU(cudaMemsetAsync(P.queue, 0, 8, s));   // the level queue and the error word
         k_peel_app<kAppNT><<<grid, kAppNT, smem, s>>>(P); note_launch();
         APP_CU(cudaGetLastError());
+        APP_CU(cudaMemcpyAsync(&herr, P.err, 4, cudaMemcpyDeviceToHost, s));
+        APP_CU(cudaStreamSynchronize(s));   // the host plans above leave scope
+        if (herr) {
+            set_error("PeelApp: a level's bucket queue disagreed with its counts (%u)", herr);
+            st = DSD_ERR_INTERNAL;
+            goto done;
+        }
         k_app_pick<<<1, 32, 0, s>>>(nl, best, pick); note_launch();
         APP_CU(cudaGetLastError());
     }
@@ -621,7 +866,7 @@ done:
                     (void*)lev, (void*)cur, (void*)ids, (void*)tmp, (void*)lenv, (void*)newlen,
                     (void*)lpos, (void*)rank_at, (void*)posof, (void*)pdeg, (void*)stepv,
                     (void*)best, (void*)pick, (void*)lorder, (void*)bigw, (void*)flag,
-                    (void*)pos, (void*)obuf})
+                    (void*)pos, (void*)obuf, (void*)qBv, (void*)qoffv, (void*)qg})
         dev_free(p, s);
     return st;
 }
