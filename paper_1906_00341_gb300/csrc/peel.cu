@@ -264,7 +264,8 @@ __device__ __forceinline__ uint32_t block_scan_count(uint32_t v, uint32_t* wtot,
 template <int NT>
 __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const uint32_t* F,
                                                      uint32_t f, unsigned long long* pre,
-                                                     unsigned long long* red) {
+                                                     unsigned long long* red,
+                                                     bool skip_empty = false) {
     constexpr int E = kSmallFront / NT;
     unsigned long long d[E], sum = 0;
     uint32_t i0 = threadIdx.x * E;
@@ -274,7 +275,8 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
         d[q] = 0;
         if (i < f) {
             uint32_t v = F[i];
-            d[q] = P.wend[v] - P.off[v];
+            // a frontier vertex of count 0 lies in no clique: no items
+            if (!skip_empty || P.deg[v] != 0) d[q] = P.wend[v] - P.off[v];
         }
         sum += d[q];
     }
@@ -739,7 +741,9 @@ __device__ __forceinline__ void hub_bitmaps(const PeelParams& P, uint32_t nhub, 
 }
 
 // P2: the cliques destroyed by frontier F (nf vertices; F in global or
-// shared memory, identical for every block).  bm: shared bitmaps of the
+// shared memory, identical for every block).  Frontier counts do not change
+// during P2 (only alive vertices are lowered), so a frontier vertex of count
+// 0, which lies in no clique of the current set, is skipped.  bm: shared bitmaps of the
 // neighbourhoods of F[0 .. min(nf, kBitmapSlots)) (small regime), or null.
 template <int NT>
 __device__ __forceinline__ void process_frontier(
@@ -754,9 +758,10 @@ __device__ __forceinline__ void process_frontier(
     const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gwarp = gtid >> 5;
     const uint64_t gwarps = gthreads >> 5;
+    if (k == 0) return;   // every frontier vertex has count 0
     if (nf <= kSmallFront) {
         // flatten (v, neighbour index) items over the whole grid
-        block_prefix_degrees<NT>(P, F, nf, s_pre, s_red);
+        block_prefix_degrees<NT>(P, F, nf, s_pre, s_red, true);
         unsigned long long T = s_pre[nf];
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             items += T;
@@ -799,6 +804,7 @@ __device__ __forceinline__ void process_frontier(
     } else if (P.h == 2) {
         for (uint64_t i = gwarp; i < nf; i += gwarps) {
             uint32_t v = F[i];
+            if (P.deg[v] == 0) continue;
             uint64_t b = P.off[v], e = P.wend[v];
             for (uint64_t p = b + lane; p < e; p += 32) {
                 uint32_t u = P.wadj[p];
@@ -827,7 +833,7 @@ __device__ __forceinline__ void process_frontier(
             for (uint32_t b0 = 0; b0 < nh; b0 += kSmallFront) {
                 const uint32_t nb = nh - b0 < kSmallFront ? nh - b0 : kSmallFront;
                 const uint32_t* H = hl + b0;
-                block_prefix_degrees<NT>(P, H, nb, s_pre, s_red);
+                block_prefix_degrees<NT>(P, H, nb, s_pre, s_red, true);
                 unsigned long long T = s_pre[nb];
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     items += T;
@@ -857,7 +863,7 @@ __device__ __forceinline__ void process_frontier(
                 const uint32_t i1 = i0 + ch < nf ? i0 + ch : nf;
                 for (uint32_t i = i0; i < i1; i++) {
                     uint32_t v = F[i];
-                    if (P.sl[v] & kHeavyBit) continue;   // taken above
+                    if ((P.sl[v] & kHeavyBit) || P.deg[v] == 0) continue;   // taken above, or none
                     uint64_t b = P.off[v], e = P.wend[v];
                     for (uint64_t p = b + wid; p < e; p += NW)
                         process_vw(P, v, P.wadj[p], k, Fnext, next_cnt, wC, wCnt, wRows, big_cnt,
@@ -872,6 +878,7 @@ __device__ __forceinline__ void process_frontier(
         }
         for (uint64_t i = blockIdx.x; i < nf; i += gridDim.x) {
             uint32_t v = F[i];
+            if (P.deg[v] == 0) continue;
             uint64_t b = P.off[v], e = P.wend[v];
             const uint32_t* vbm = (bm && i < kBitmapSlots) ? bm + (size_t)i * bm_words : nullptr;
             for (uint64_t p = b + wid; p < e; p += NW)
