@@ -62,6 +62,12 @@ constexpr uint32_t kBitmapSlots = 16;   // frontier vertices with a shared bitma
 constexpr int kChunks = 4;              // 32-entry chunks of a row in flight per warp
 constexpr uint32_t kWarpCand = 32;      // candidate sets a warp handles itself (h >= 4)
 constexpr uint32_t kWarpWords = 3 * kWarpCand;   // a warp's candidates, counters, rows
+// h >= 4: a warp lists the cliques of a candidate set of at most this many
+// vertices itself; larger sets go to a whole block after the next grid
+// barrier.  Items are the round's critical path when one warp walks the rows
+// of many candidates in turn: on R-MAT scale 21 the peel took 9.4 s (h = 4)
+// and 20.5 s (h = 5) with the limit at 32, 5.2 s and 13.5 s at 4.
+__host__ __device__ inline uint32_t warp_cand_limit(int h) { return h >= 4 ? 4u : kWarpCand; }
 constexpr uint32_t kHeavyBit = 4;       // state word: frontier vertex on the heavy list
 constexpr uint32_t kSlotShift = 3;      // state word: 1 + its neighbourhood bitmap slot
 constexpr uint32_t kSlotMask = 0xffu;
@@ -156,6 +162,8 @@ struct PeelParams {
     unsigned long long k0; // initial level: kstart - 1, or 0
     uint32_t cap;          // candidate sets are at most this (>= max |N+|, >= 32)
     uint32_t bcap;         // a big item's shared buffers: min(cap, kBitmapMax)
+    uint32_t warp_cand;    // h >= 4: candidate sets a warp handles (<= kWarpCand); larger
+                           // ones go to a block
     uint32_t* xl;          // per block (kMaxDepth + 1) * cap entries when cap > kBitmapMax
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
@@ -309,7 +317,7 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
 //   kGatherDirect (h = 3): each candidate closes the triangle {v, w, x}; an
 //     alive candidate loses it on the spot; nothing is stored;
 //   kGatherWarp: the first kWarpCand candidates go to C; the walk stops as
-//     soon as there are more (the item then needs a block).
+//     soon as there are more than P.warp_cand (the item then needs a block).
 // gbm (large regime, may be null): v's neighbourhood bitmap over vertex ids.
 // Returns the number of candidates seen.
 enum { kGatherDirect = 0, kGatherWarp = 1 };
@@ -382,7 +390,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
                 }
                 take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
             }
-            if (MODE == kGatherWarp && nc > kWarpCand) return nc;
+            if (MODE == kGatherWarp && nc > P.warp_cand) return nc;
         }
         return nc;
     }
@@ -422,7 +430,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
             }
             take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
         }
-        if (MODE == kGatherWarp && nc > kWarpCand) return nc;
+        if (MODE == kGatherWarp && nc > P.warp_cand) return nc;
     }
     return nc;
 }
@@ -430,7 +438,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
 // One (v, w) work item of a frontier vertex v with h >= 3: the cliques
 // {v, w, ...} whose members other than v are candidates of v and whose
 // smallest such member is w.  Executed by one warp; C, cnt, rows are the
-// warp's kWarpCand-entry buffers.  Candidate sets above kWarpCand (h >= 4)
+// warp's kWarpCand-entry buffers.  Candidate sets above P.warp_cand (h >= 4)
 // are queued as big items for a block.
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
@@ -451,7 +459,7 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
             gather_candidates<kGatherWarp>(P, v, w, C, bm, gbm, k, next, next_cnt, bytes);
         __syncwarp();
         if (nc < (uint32_t)r) return;
-        if (nc > kWarpCand) {
+        if (nc > P.warp_cand) {
             if (lane == 0) {
                 uint32_t at = atomicAdd(big_cnt, 1u);
                 if (at < P.big_cap) P.big[at] = make_uint2(v, w);
@@ -1563,6 +1571,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.snap = snap;
     P.cap = maxdplus < 32 ? 32 : maxdplus;
     P.bcap = P.cap < kBitmapMax ? P.cap : kBitmapMax;
+    P.warp_cand = warp_cand_limit(h);
     P.compact = h >= 3 ? 1 : 0;
     // Big items (candidate sets above kWarpCand vertices, one block each)
     // for h >= 4; every candidate set fits 32-word rows.
