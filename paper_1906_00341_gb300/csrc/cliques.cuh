@@ -73,6 +73,34 @@ __device__ __forceinline__ unsigned scan_row_hits(const uint32_t* C, uint32_t nc
     return hits;
 }
 
+// One warp: the one-word row of candidate x = C[i] for |C| <= 32, i.e. bit j
+// set iff C[j] > x lies in x's list adj[b, e) (sorted ascending; the scan
+// stops past cmax = C[nc - 1]).  All lanes return it.
+__device__ __forceinline__ uint32_t warp_row32(const uint32_t* C, uint32_t nc, uint32_t cmax,
+                                               uint32_t x, const uint32_t* adj, uint64_t b,
+                                               uint64_t e) {
+    const unsigned lane = lane_id();
+    uint32_t bits = 0;
+    for (uint64_t p0 = b; p0 < e; p0 += 32 * kScanChunks) {
+        uint32_t ys[kScanChunks];
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            uint64_t p = p0 + u * 32 + lane;
+            ys[u] = p < e ? adj[p] : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < kScanChunks; u++) {
+            const uint32_t y = ys[u];
+            if (y > x && y <= cmax) {
+                uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
+                if (pos < nc && C[pos] == y) bits |= 1u << pos;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) break;
+    }
+    return __reduce_or_sync(0xffffffffu, bits);
+}
+
 // Warp builds one-word rows for |C| <= 32 (rows[i] for i < nc).  The last
 // candidate's row is empty (no candidate lies above it).
 template <class OFF>
@@ -84,26 +112,7 @@ __device__ __forceinline__ void warp_build_rows32(const uint32_t* C, uint32_t nc
     const uint32_t cmax = C[nc - 1];
     for (uint32_t i = 0; i + 1 < nc; i++) {
         const uint32_t x = C[i];
-        const uint64_t b = nb[x], e = ne[x];
-        uint32_t bits = 0;
-        for (uint64_t p0 = b; p0 < e; p0 += 32 * kScanChunks) {
-            uint32_t ys[kScanChunks];
-#pragma unroll
-            for (int u = 0; u < kScanChunks; u++) {
-                uint64_t p = p0 + u * 32 + lane;
-                ys[u] = p < e ? adj[p] : 0xffffffffu;
-            }
-#pragma unroll
-            for (int u = 0; u < kScanChunks; u++) {
-                const uint32_t y = ys[u];
-                if (y > x && y <= cmax) {
-                    uint32_t pos = (uint32_t)lower_bound_u32(C, nc, y);
-                    if (pos < nc && C[pos] == y) bits |= 1u << pos;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, ys[kScanChunks - 1], 31) > cmax) break;
-        }
-        bits = __reduce_or_sync(0xffffffffu, bits);
+        const uint32_t bits = warp_row32(C, nc, cmax, x, adj, nb[x], ne[x]);
         if (lane == 0) rows[i] = bits;
     }
     if (lane == 0) rows[nc - 1] = 0;

@@ -62,6 +62,8 @@ constexpr uint32_t kBitmapSlots = 16;   // frontier vertices with a shared bitma
 constexpr int kChunks = 4;              // 32-entry chunks of a row in flight per warp
 constexpr uint32_t kWarpCand = 32;      // candidate sets a warp handles itself (h >= 4)
 constexpr uint32_t kWarpWords = 3 * kWarpCand;   // a warp's candidates, counters, rows
+constexpr uint32_t kMidWords = 3 + kWarpCand;    // a mid item: v, w, |C|, C
+constexpr int kGroupWarps = 8;                    // warps of a group taking one mid item
 // h >= 4: a warp lists the cliques of a candidate set of at most this many
 // vertices itself; larger sets go to a whole block after the next grid
 // barrier.  Items are the round's critical path when one warp walks the rows
@@ -78,13 +80,13 @@ struct PeelCtrl {
     unsigned long long min_deg[2];
     uint32_t new_alive[2];
     uint32_t fcnt[3];
-    uint32_t big_cnt[3];
+    uint32_t big_cnt[6];            // per round slot s: big items [s], mid items [3 + s]
     unsigned long long destroyed[3];
     uint32_t hcnt[3];               // heavy frontier vertices of the round
     uint32_t grab[3];               // light frontier vertices taken by blocks
-    uint32_t bgrab[3];              // big items taken by blocks
+    uint32_t bgrab[6];              // big items [s] and mid items [3 + s] taken
     uint32_t hubcnt[2];             // bitmap slots asked for, by round parity
-    uint32_t pad0[5];
+    uint32_t pad0[11];
     uint32_t bar_count;
     uint32_t pad1[31];
     uint32_t bar_gen;
@@ -163,7 +165,10 @@ struct PeelParams {
     uint32_t cap;          // candidate sets are at most this (>= max |N+|, >= 32)
     uint32_t bcap;         // a big item's shared buffers: min(cap, kBitmapMax)
     uint32_t warp_cand;    // h >= 4: candidate sets a warp handles (<= kWarpCand); larger
-                           // ones go to a block
+                           // ones go to a warp group (mid items) or a block
+    uint32_t gather_cap;   // a warp's candidate walk stops past this many
+    uint32_t* mid;         // mid items: kMidWords words each (v, w, |C|, C)
+    uint32_t mid_cap;      // 0: none (every set above warp_cand goes to a block)
     uint32_t* xl;          // per block (kMaxDepth + 1) * cap entries when cap > kBitmapMax
     int compact;           // drop removed vertices from rows as the graph shrinks
     uint32_t work_words;   // shared words before the small-regime lists
@@ -317,7 +322,7 @@ __device__ __forceinline__ void block_prefix_degrees(const PeelParams& P, const 
 //   kGatherDirect (h = 3): each candidate closes the triangle {v, w, x}; an
 //     alive candidate loses it on the spot; nothing is stored;
 //   kGatherWarp: the first kWarpCand candidates go to C; the walk stops as
-//     soon as there are more than P.warp_cand (the item then needs a block).
+//     soon as there are more than P.gather_cap (the item then needs a block).
 // gbm (large regime, may be null): v's neighbourhood bitmap over vertex ids.
 // Returns the number of candidates seen.
 enum { kGatherDirect = 0, kGatherWarp = 1 };
@@ -390,7 +395,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
                 }
                 take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
             }
-            if (MODE == kGatherWarp && nc > P.warp_cand) return nc;
+            if (MODE == kGatherWarp && nc > P.gather_cap) return nc;
         }
         return nc;
     }
@@ -430,7 +435,7 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
             }
             take_candidate<MODE>(P, ok, s == kAlive, x, C, nc, k, next, next_cnt, bytes);
         }
-        if (MODE == kGatherWarp && nc > P.warp_cand) return nc;
+        if (MODE == kGatherWarp && nc > P.gather_cap) return nc;
     }
     return nc;
 }
@@ -439,7 +444,8 @@ __device__ __forceinline__ uint32_t gather_candidates(const PeelParams& P, uint3
 // {v, w, ...} whose members other than v are candidates of v and whose
 // smallest such member is w.  Executed by one warp; C, cnt, rows are the
 // warp's kWarpCand-entry buffers.  Candidate sets above P.warp_cand (h >= 4)
-// are queued as big items for a block.
+// are queued, as mid items with their candidates when at most kWarpCand
+// (`big_cnt + 3` counts them), else as big items for a block.
 __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned long long k,
                            uint32_t* next, uint32_t* next_cnt, uint32_t* C, unsigned* cnt,
                            uint32_t* rows, uint32_t* big_cnt, const uint32_t* bm,
@@ -460,6 +466,23 @@ __device__ void process_vw(const PeelParams& P, uint32_t v, uint32_t w, unsigned
         __syncwarp();
         if (nc < (uint32_t)r) return;
         if (nc > P.warp_cand) {
+            // mid item: its candidates go with it to a warp group; else a block
+            if (nc <= kWarpCand && P.mid_cap) {
+                uint32_t at = 0;
+                if (lane == 0) at = atomicAdd(big_cnt + 3, 1u);
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (at < P.mid_cap) {
+                    uint32_t* rec = P.mid + (size_t)at * kMidWords;
+                    if (lane < nc) rec[3 + lane] = C[lane];
+                    if (lane == 0) {
+                        rec[0] = v;
+                        rec[1] = w;
+                        rec[2] = nc;
+                        bytes += 12 + 4ull * nc;
+                    }
+                    return;
+                }
+            }
             if (lane == 0) {
                 uint32_t at = atomicAdd(big_cnt, 1u);
                 if (at < P.big_cap) P.big[at] = make_uint2(v, w);
@@ -658,6 +681,84 @@ bitmap:
         }
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void group_bar(uint32_t id, uint32_t threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Mid items (h >= 4; candidate sets of warp_cand + 1 .. 32 vertices, listed
+// by the warp that found them): groups of kGroupWarps warps take them from
+// *grab, several per block at once.  The group's warps build the one-word
+// rows of G[C] side by side (one candidate's list each), its first warp
+// lists the cliques of G[C] (warp_dfs32), and the alive members are lowered.
+// Group g synchronises on named barrier 1 + g.  destroyed: the round's sum.
+template <int NT>
+__device__ void drain_mid(const PeelParams& P, uint32_t nm, uint32_t* grab, unsigned long long k,
+                          uint32_t* next, uint32_t* next_cnt, unsigned long long* destroyed,
+                          unsigned long long& bytes) {
+    constexpr int NG = NT / 32 / kGroupWarps;
+    struct MidBuf {
+        uint32_t C[kWarpCand];
+        unsigned cnt[kWarpCand];
+        uint32_t rows[kWarpCand];
+        uint32_t i;
+        unsigned long long tot;
+    };
+    __shared__ MidBuf s_mb[NG];
+    const unsigned lane = lane_id(), wid = warp_id();
+    const uint32_t grp = wid / kGroupWarps, gw = wid % kGroupWarps;
+    const uint32_t bar = 1u + grp, nth = kGroupWarps * 32u;
+    MidBuf& B = s_mb[grp];
+    const int r = P.h - 2;
+    unsigned long long dsum = 0;
+    for (;;) {
+        if (gw == 0 && lane == 0) B.i = atomicAdd(grab, 1u);
+        group_bar(bar, nth);
+        const uint32_t i = B.i;
+        if (i >= nm) break;
+        const uint32_t* rec = P.mid + (size_t)i * kMidWords;
+        const uint32_t v = rec[0], w = rec[1], nc = rec[2];
+        (void)v;
+        if (gw == 0) {
+            B.C[lane] = lane < nc ? rec[3 + lane] : 0u;
+            B.cnt[lane] = 0;
+            B.rows[lane] = 0;
+        }
+        group_bar(bar, nth);
+        const uint32_t cmax = B.C[nc - 1];
+        for (uint32_t x = gw; x + 1 < nc; x += kGroupWarps) {
+            const uint32_t y = B.C[x];
+            const uint32_t bits = warp_row32(B.C, nc, cmax, y, P.wadj, P.wnb[y], P.wend[y]);
+            if (lane == 0) {
+                B.rows[x] = bits;
+                bytes += 16 + 4ull * (P.wend[y] - P.wnb[y]);
+            }
+        }
+        group_bar(bar, nth);
+        if (gw == 0) {
+            const unsigned long long t = warp_dfs32(B.rows, nc, r, B.cnt);
+            if (lane == 0) B.tot = t;
+        }
+        group_bar(bar, nth);
+        const unsigned long long tot = B.tot;
+        if (tot) {
+            const uint32_t t = gw * 32 + lane;
+            if (t < nc && B.cnt[t]) {
+                const uint32_t x = B.C[t];
+                if (st_of(P.sl[x]) == kAlive) {
+                    dec_and_queue(P, x, (unsigned long long)B.cnt[t], k, next, next_cnt);
+                    bytes += 20;
+                }
+            }
+            if (gw == 0 && lane == 0) {
+                if (st_of(P.sl[w]) == kAlive) dec_and_queue(P, w, tot, k, next, next_cnt);
+                dsum += tot;
+            }
+        }
+        group_bar(bar, nth);   // B is rewritten by the next item
+    }
+    if (gw == 0 && lane == 0 && dsum) atomicAdd(destroyed, dsum);
 }
 
 // Drop removed vertices from row v in place (one warp); rows stay sorted.
@@ -1026,6 +1127,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                     c->destroyed[(r + 2) % 3] = 0;
                     c->big_cnt[(r + 2) % 3] = 0;
                     c->bgrab[(r + 2) % 3] = 0;
+                    c->big_cnt[3 + (r + 2) % 3] = 0;
+                    c->bgrab[3 + (r + 2) % 3] = 0;
                 }
                 c->fcnt[(r + 1) % 3] = 0;
                 c->hcnt[(r + 1) % 3] = 0;
@@ -1148,8 +1251,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 // ------------------------------------------------- P2b
                 if (P.big_cap) {
                     uint32_t nb = c->big_cnt[r % 3];
-                    if (nb) {
+                    uint32_t nm = c->big_cnt[3 + r % 3];
+                    if (nb || nm) {
                         if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
+                        if (nm > P.mid_cap) nm = P.mid_cap;
+                        if (nm) {
+                            drain_mid<NT>(P, nm, &c->bgrab[3 + r % 3], k, P.front[(r + 1) % 3],
+                                          &c->fcnt[(r + 1) % 3], &c->destroyed[r % 3], bytes);
+                            __syncthreads();
+                        }
                         unsigned long long d2 = 0;
                         for (;;) {
                             if (threadIdx.x == 0) s_grab = atomicAdd(&c->bgrab[r % 3], 1u);
@@ -1186,6 +1296,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
                 c->destroyed[(r + 2) % 3] = 0;
                 c->big_cnt[(r + 2) % 3] = 0;
                 c->bgrab[(r + 2) % 3] = 0;
+                c->big_cnt[3 + (r + 2) % 3] = 0;
+                c->bgrab[3 + (r + 2) % 3] = 0;
             }
             uint32_t nf_new = c->fcnt[r % 3];
             __syncthreads();
@@ -1370,8 +1482,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_peel(PeelParams P) {
             BARRIER(7);
             if (P.big_cap) {
                 uint32_t nb = c->big_cnt[r % 3];
-                if (nb) {
+                uint32_t nm = c->big_cnt[3 + r % 3];
+                if (nb || nm) {
                     if (nb > P.big_cap) nb = (uint32_t)P.big_cap;
+                    if (nm > P.mid_cap) nm = P.mid_cap;
+                    if (nm) {
+                        drain_mid<NT>(P, nm, &c->bgrab[3 + r % 3], k, P.front[(r + 1) % 3],
+                                      &c->fcnt[(r + 1) % 3], &c->destroyed[r % 3], bytes);
+                        __syncthreads();
+                    }
                     unsigned long long d2 = 0;
                     for (;;) {
                         if (threadIdx.x == 0) s_grab = atomicAdd(&c->bgrab[r % 3], 1u);
@@ -1572,6 +1691,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     P.cap = maxdplus < 32 ? 32 : maxdplus;
     P.bcap = P.cap < kBitmapMax ? P.cap : kBitmapMax;
     P.warp_cand = warp_cand_limit(h);
+    P.gather_cap = P.warp_cand;
     P.compact = h >= 3 ? 1 : 0;
     // Big items (candidate sets above kWarpCand vertices, one block each)
     // for h >= 4; every candidate set fits 32-word rows.
@@ -1634,6 +1754,7 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     PeelCtrl* ctrl = nullptr;
     uint32_t* rows_g = nullptr;
     uint2* big = nullptr;
+    uint32_t* mid = nullptr;
     uint32_t* heavy = nullptr;
     uint32_t* xl = nullptr;
     uint32_t* hub_bm = nullptr;
@@ -1656,6 +1777,15 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
     if (big_items) {
         P.big_cap = g->m * 2 + 1;
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
+        // mid items (sets of warp_cand + 1 .. 32 candidates): up to 2^20 per
+        // round (144 MB), the rest as big items
+        const uint64_t mc = P.big_cap < (1u << 20) ? P.big_cap : (1u << 20);
+        if (P.warp_cand < kWarpCand) {
+            if ((st = dalloc(&mid, (size_t)mc * kMidWords, s)) != DSD_OK) goto done;
+            P.mid = mid;
+            P.mid_cap = (uint32_t)mc;
+            P.gather_cap = kWarpCand;
+        }
     }
     if (P.heavy_min && (st = dalloc(&heavy, n, s)) != DSD_OK) goto done;
     P.heavy = heavy;
@@ -1772,6 +1902,7 @@ done:
     dev_free(ctrl, s);
     dev_free(rows_g, s);
     dev_free(big, s);
+    dev_free(mid, s);
     dev_free(heavy, s);
     dev_free(xl, s);
     dev_free(hub_bm, s);
