@@ -34,7 +34,8 @@ struct CountArgs {
     unsigned long long* mu;
     uint32_t* listM;      // vertices of tier M
     uint32_t* listL;      // vertices of tier L
-    uint32_t* cntML;      // [0] tier M, [1] tier L, [3] checked-mode overflow
+    uint32_t* cntML;      // [0] tier M, [1] tier L, [3] checked-mode overflow, [4] tier S
+                          // chunks taken, [5] tier M and [6] tier L vertices taken
     uint32_t* work;       // [1] dynamic queue for tier S
     uint32_t* ovf;        // checked mode: set when a counter wraps (else null)
 };
@@ -111,9 +112,15 @@ __global__ void __launch_bounds__(NT) k_count_medium(CountArgs A) {
     uint32_t* C = smem + 2 * kBitmapMax;      // 1024
     uint32_t* rows = smem + 3 * kBitmapMax;   // up to 1024*32 (only if r >= 3)
     __shared__ unsigned long long s_tot;
-    __shared__ uint32_t s_next;
+    __shared__ uint32_t s_next, s_it;
     uint32_t nM = A.cntML[0];
-    for (uint32_t it = blockIdx.x; it < nM; it += gridDim.x) {
+    // vertices are taken one at a time from a shared counter: their work
+    // varies by orders of magnitude
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(&A.cntML[5], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        if (it >= nM) break;
         uint32_t u = A.listM[it];
         uint64_t b = A.split[u], e = A.off[u + 1];
         uint32_t d = (uint32_t)(e - b);
@@ -161,9 +168,14 @@ __global__ void __launch_bounds__(NT) k_count_medium(CountArgs A) {
 // the credits go straight to the global counters.
 __global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
     __shared__ unsigned long long s_tot;
+    __shared__ uint32_t s_it;
     uint32_t nL = A.cntML[1];
     unsigned lane = lane_id(), nw = blockDim.x >> 5;
-    for (uint32_t it = blockIdx.x; it < nL; it += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(&A.cntML[6], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        if (it >= nL) break;
         uint32_t u = A.listL[it];
         uint64_t b = A.split[u], e = A.off[u + 1];
         uint32_t d = (uint32_t)(e - b);
@@ -202,9 +214,14 @@ __global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
 __global__ void __launch_bounds__(1024) k_count_xl(CountArgs A, uint32_t* scratch, uint32_t cap) {
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_root;
+    __shared__ uint32_t s_it;
     uint32_t* mine = scratch + (size_t)blockIdx.x * kMaxDepth * cap;
     const uint32_t nL = A.cntML[1];
-    for (uint32_t it = blockIdx.x; it < nL; it += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(&A.cntML[6], 1u);
+        __syncthreads();
+        const uint32_t it = s_it;
+        if (it >= nL) break;
         const uint32_t u = A.listL[it];
         const uint64_t b = A.split[u], e = A.off[u + 1];
         if (threadIdx.x == 0) s_root = 0;
