@@ -164,6 +164,43 @@ __global__ void __launch_bounds__(NT) k_count_medium(CountArgs A) {
     }
 }
 
+// Tier M in decreasing |N+(u)|, so that the largest searches start first and
+// the last vertices taken are short: a counting sort over d in (32, 1024]
+// (order inside one d is arbitrary; the counts do not depend on it).
+__global__ void k_m_hist(CountArgs A, uint32_t* hist) {
+    const uint32_t nM = A.cntML[0];
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nM; it += gridDim.x * blockDim.x) {
+        const uint32_t u = A.listM[it];
+        const uint32_t d = (uint32_t)(A.off[u + 1] - A.split[u]);
+        atomicAdd(&hist[kBitmapMax - d], 1u);
+    }
+}
+// one block of kBitmapMax threads: hist -> exclusive starts
+__global__ void __launch_bounds__(kBitmapMax) k_m_starts(uint32_t* hist) {
+    __shared__ uint32_t s_w[kBitmapMax / 32];
+    const unsigned lane = lane_id(), wid = warp_id();
+    const uint32_t x = hist[threadIdx.x];
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (unsigned w = 0; w < wid; w++) before += s_w[w];
+    hist[threadIdx.x] = before + inc - x;
+}
+__global__ void k_m_place(CountArgs A, uint32_t* start, uint32_t* out) {
+    const uint32_t nM = A.cntML[0];
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < nM; it += gridDim.x * blockDim.x) {
+        const uint32_t u = A.listM[it];
+        const uint32_t d = (uint32_t)(A.off[u + 1] - A.split[u]);
+        out[atomicAdd(&start[kBitmapMax - d], 1u)] = u;
+    }
+}
+
 // Tier L (h = 3 only): |N+(u)| > 1024; candidates stay in global memory and
 // the credits go straight to the global counters.
 __global__ void __launch_bounds__(kCountThreads) k_count_large3(CountArgs A) {
@@ -306,7 +343,7 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     A.mu = mu_dev;
     uint32_t* ws = nullptr;
     uint32_t* xl_scratch = nullptr;
-    DSD_TRY(dalloc(&ws, (size_t)2 * n + 8, s));
+    DSD_TRY(dalloc(&ws, (size_t)3 * n + 8 + kBitmapMax, s));
     A.listM = ws;
     A.listL = ws + n;
     A.cntML = ws + 2 * (size_t)n;
@@ -316,6 +353,19 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
     cudaError_t e = cudaMemsetAsync(A.cntML, 0, 8 * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         k_count_small<<<sms * 8, kCountThreads, 0, s>>>(A); note_launch();
+        {
+            // tier M by decreasing |N+(u)|
+            uint32_t* hist = A.cntML + 8;
+            uint32_t* sorted = hist + kBitmapMax;
+            e = cudaMemsetAsync(hist, 0, kBitmapMax * sizeof(uint32_t), s);
+            if (e == cudaSuccess) {
+                k_m_hist<<<sms * 4, 256, 0, s>>>(A, hist);
+                k_m_starts<<<1, kBitmapMax, 0, s>>>(hist);
+                k_m_place<<<sms * 4, 256, 0, s>>>(A, hist, sorted);
+                for (int i = 0; i < 3; i++) note_launch();
+                A.listM = sorted;
+            }
+        }
         size_t smemM = (size_t)3 * kBitmapMax * 4 + (h >= 4 ? (size_t)kBitmapMax * 32 * 4 : 0);
         if (h >= 4) {
             // one block per SM (the rows fill its shared memory): 32 warps
@@ -353,7 +403,7 @@ dsd_status count_cliques(dsd_graph* g, int h, unsigned long long* deg_new,
         set_error("h=%d: a clique-degree or mu exceeds 2^64 - 1 (checked mode)", h);
         return DSD_ERR_OVERFLOW;
     }
-    g->prof_launches[kPhaseCount] = h == 3 ? 3 : (g->maxdplus > kBitmapMax ? 3 : 2);
+    g->prof_launches[kPhaseCount] = h == 3 ? 6 : (g->maxdplus > kBitmapMax ? 6 : 5);
     return st;
 }
 
