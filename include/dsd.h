@@ -99,6 +99,15 @@ dsd_status dsd_set_peel_small_limit(uint32_t max_alive);
  * memory below about 4,600; the default is as large as those hold; 0 =
  * never).  Results do not depend on it.  Process-wide. */
 dsd_status dsd_set_peel_tail_limit(uint32_t max_alive);
+/* Where dsd_peel_app keeps each level's bucket queue (the bitmaps, one per
+ * count below k + 1, over the level's positions): in a block's shared memory
+ * when it fits `shared_words` 32-bit words (default and maximum 12,288), else
+ * in global memory while the levels placed there total at most
+ * `global_words` words (default 2^26), else only the buckets of the smallest
+ * counts that fit shared memory, with a scan of the level behind them (0 and
+ * 0: the scan alone).  Results do not depend on it.  Process-wide; applies
+ * to calls started afterwards.  Never fails. */
+dsd_status dsd_set_peel_app_queue(uint32_t shared_words, uint64_t global_words);
 
 /* Checked mode (off by default; process-wide, for calls started
  * afterwards).  Clique-degrees and mu are exact unsigned 64-bit integers;

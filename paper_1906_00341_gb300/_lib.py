@@ -89,6 +89,7 @@ SIGNATURES = {
     "dsd_set_wait_limit_ms": (_int, [_u32]),
     "dsd_set_peel_small_limit": (_int, [_u32]),
     "dsd_set_peel_tail_limit": (_int, [_u32]),
+    "dsd_set_peel_app_queue": (_int, [_u32, ctypes.c_uint64]),
     "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_destroy": (None, [_P]),
@@ -224,6 +225,10 @@ def dsd_set_peel_small_limit(max_alive):
 
 def dsd_set_peel_tail_limit(max_alive):
     _check(load().dsd_set_peel_tail_limit(max_alive))
+
+
+def dsd_set_peel_app_queue(shared_words, global_words):
+    _check(load().dsd_set_peel_app_queue(shared_words, global_words))
 
 
 def dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr):

@@ -18,6 +18,11 @@ uint32_t peel_small_limit() { return g_small_limit.load(); }
 static std::atomic<uint32_t> g_tail_limit{1u << 30};
 uint32_t peel_tail_limit() { return g_tail_limit.load(); }
 
+static std::atomic<uint32_t> g_app_qshared{12288};
+static std::atomic<unsigned long long> g_app_qglobal{64ull << 20};
+uint32_t peel_app_queue_shared() { return g_app_qshared.load(); }
+uint64_t peel_app_queue_global() { return g_app_qglobal.load(); }
+
 static std::atomic<int> g_checked{0};
 bool checked_mode() { return g_checked.load() != 0; }
 
@@ -358,6 +363,12 @@ dsd_status dsd_set_peel_small_limit(uint32_t max_alive) {
 
 dsd_status dsd_set_peel_tail_limit(uint32_t max_alive) {
     g_tail_limit = max_alive;
+    return DSD_OK;
+}
+
+dsd_status dsd_set_peel_app_queue(uint32_t shared_words, uint64_t global_words) {
+    g_app_qshared = shared_words < 12288 ? shared_words : 12288;
+    g_app_qglobal = global_words;
     return DSD_OK;
 }
 

@@ -56,6 +56,8 @@ void note_launch();
 uint32_t peel_small_limit();
 // Largest alive set handed to the cluster tail kernel (0 = never).
 uint32_t peel_tail_limit();
+uint32_t peel_app_queue_shared();   // PeelApp bucket queues: shared-memory words per block
+uint64_t peel_app_queue_global();   // and global-memory words in all
 
 // --------------------------------------------------------- device utils
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -743,13 +743,14 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
         // bucket queues: in shared memory after the scratch where they fit
         // (every count 0..k), else in global memory within a budget, else
         // the buckets that fit shared memory with the scan behind them
-        const size_t qsh = std::min<size_t>(12288, 220 * 1024 / 4 > words ? 220 * 1024 / 4 - words : 0);
+        const size_t qsh = std::min<size_t>(peel_app_queue_shared(),
+                                            220 * 1024 / 4 > words ? 220 * 1024 / 4 - words : 0);
         P.scratch_words = (uint32_t)words;
         P.qwords = (uint32_t)qsh;
         hqB.assign(nl, 0u);
         hqoff.assign(nl, kQShared);
         uint64_t gwords = 0;
-        const uint64_t gbudget = (uint64_t)64 << 20;   // words (256 MB)
+        const uint64_t gbudget = peel_app_queue_global();   // words (default 2^26: 256 MB)
         for (uint32_t j = 0; j < nl; j++) {
             const uint32_t sz = hls[j] - (j + 1 < nl ? hls[j + 1] : 0u);
             if (hk[j] == 0 || sz == 0 || sz > (1u << 20)) continue;   // the warp search: <= 32^4

@@ -70,3 +70,21 @@ def test_peelapp_closed_forms(L, orc):
 def test_peelapp_cl50k(L, orc):
     n, s, d, _ = gg.workload("cl50k")
     check(L, orc, n, s, d, 3)
+
+
+@pytest.mark.parametrize("shared,glob", [(0, 0), (64, 1 << 26), (600, 0), (2000, 3000)])
+def test_peelapp_queue_placements(L, orc, shared, glob):
+    """Every placement of the per-level bucket queues gives the oracle's
+    order: no queue (a scan of the level per step), queues in global memory
+    (a tiny shared budget), the buckets of the smallest counts only with the
+    scan behind them, and a global budget that runs out part way."""
+    L.dsd_set_peel_app_queue(shared, glob)
+    try:
+        n, s, d, _ = gg.plant(3000, *gg.chung_lu(3000, 24000, 2.1, 200.0, 17)[1:], 35, 0.7, 18)
+        for h in (3, 4):
+            check(L, orc, n, s, d, h)
+        for seed in range(3):
+            n, s, d = gg.random_small(120 + 40 * seed, 0.2, seed=640 + seed)
+            check(L, orc, n, s, d, 3)
+    finally:
+        L.dsd_set_peel_app_queue(12288, 1 << 26)
