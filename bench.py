@@ -687,6 +687,54 @@ def run_exact(args, local):
     }
 
 
+# ------------------------------------------------------ small ER graph, h = 2
+
+def run_c1(args, local):
+    """The sparse Erdos-Renyi configuration (n = 2000, p = 0.005, h = 2): CSR
+    build from the device edge list + dsd_core_app per call, CUDA events,
+    median of 20 calls after 3."""
+    import torch
+    from paper_1906_00341_gb300 import graphgen as gg
+    from paper_1906_00341_gb300 import _lib as L
+    L.load()
+    dev = torch.device("cuda", local)
+    n, s, d, _ = gg.workload("er2000")
+    desc = "erdos_renyi n=2000 p=0.005 seed 0, h=2"
+    src = torch.from_numpy(s.astype(np.int32)).to(dev)
+    dst = torch.from_numpy(d.astype(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    kc = torch.empty(n, dtype=torch.int32, device=dev)
+    de = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def call():
+        g = L.dsd_graph_from_edges(n, s.size, src.data_ptr(), dst.data_ptr(), L.DSD_MEM_DEVICE, sp)
+        r = L.dsd_core_app(g, 2, kc.data_ptr(), de.data_ptr(), L.DSD_MEM_DEVICE)
+        return g, r
+
+    for _ in range(3):
+        g, r = call()
+        L.dsd_graph_destroy(g)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g, r = call()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        n_, m_und = L.dsd_graph_info(g)
+        L.dsd_graph_destroy(g)
+    ms = float(np.median(times))
+    return {"workload": desc, "n": n, "m": int(m_und), "h": 2, "call_ms": ms,
+            "h_cliques_per_s": int(m_und) / (ms / 1e3), "kmax": int(r.kmax),
+            "densest": [int(r.densest_mu), int(r.densest_size)],
+            "timing": "CUDA events around dsd_graph_from_edges + dsd_core_app (device edge "
+                      "list and outputs), median of 20 calls after 3; a launch-bound size"}
+
+
 # ------------------------------------------------------ R-MAT scale 22
 
 def listing_roofline(L, hnd, count_ms, peak, peak_kind, traffic_key=None):
@@ -838,6 +886,7 @@ def main():
             line["exact"] = run_exact(args, local)
         if not args.no_c3:
             line["c3"] = run_c3(args, local)
+        line["c1"] = run_c1(args, local)
         if not args.no_cpu_baseline and world == 1:
             t, smu, _ = time_oracle(n, s, d, h)
             line["cpu_baseline"] = {
