@@ -13,6 +13,8 @@
 // N+(v) = {u in N(v) : u > v} is the tail of row v (start kept in rsplit).
 #include "graph.cuh"
 
+#include <vector>
+
 namespace dsd {
 namespace {
 
@@ -35,6 +37,23 @@ __global__ void k_round_scatter(uint32_t n, const uint32_t* rnd, const uint64_t*
         uint32_t r = rnd[v];
         out[start[r] + atomicAdd(&cursor[r], 1u)] = (uint32_t)v;
     }
+}
+
+// A round of more than kHugeRound members: flag[v] = 1 iff v left in it; the
+// members then go to their place in id order through a scan of the flags
+// (1M-vertex Chung-Lu graph: orientation 5.4 -> 3.1 ms at this threshold,
+// 3.9 ms at 65,536; each such round costs a handful of launches).
+constexpr uint32_t kHugeRound = 16384;
+__global__ void k_round_flag(uint32_t n, const uint32_t* rnd, uint32_t r, uint32_t* flag) {
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x)
+        flag[v] = rnd[v] == r ? 1u : 0u;
+}
+__global__ void k_round_place(uint32_t n, const uint32_t* rnd, uint32_t r, const uint64_t* pos,
+                              const uint64_t* start, uint32_t* out) {
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x)
+        if (rnd[v] == r) out[start[r] + pos[v]] = (uint32_t)v;
 }
 
 __global__ void k_invert(uint32_t n, const uint32_t* old_of, uint32_t* new_of,
@@ -98,6 +117,7 @@ dsd_status ensure_order(dsd_graph* g) {
     uint32_t* tmp = nullptr;
     uint32_t* dmax = nullptr;
     PeelResult pr;
+    std::vector<uint32_t> hh;
     uint32_t R = 0;
     uint32_t hmax = 0;
 #define STEP(x)                      \
@@ -156,6 +176,22 @@ dsd_status ensure_order(dsd_graph* g) {
     CUSTEP(cudaMemsetAsync(rdeg, 0, ((size_t)n + 1) * 4, s));
     k_round_scatter<<<grid, 256, 0, s>>>(n, g->rnd, start, rdeg, g->old_of); note_launch();
     CUSTEP(cudaGetLastError());
+    // the largest rounds (the first ones of a large graph) in id order by a
+    // flag scan over all vertices, each over the whole GPU, rather than by the
+    // row sort's one block per row; their rows are then left out of the sort
+    hh.resize(R);
+    CUSTEP(cudaMemcpyAsync(hh.data(), hist, (size_t)R * 4, cudaMemcpyDeviceToHost, s));
+    CUSTEP(cudaStreamSynchronize(s));
+    for (uint32_t r = 0; r < R; r++) {
+        if (hh[r] <= kHugeRound) continue;
+        uint64_t* fpos = reinterpret_cast<uint64_t*>(deg);   // free after the peel
+        k_round_flag<<<grid, 256, 0, s>>>(n, g->rnd, r, tmp); note_launch();
+        CUSTEP(cudaGetLastError());
+        STEP(exclusive_scan_u32_to_u64(tmp, fpos, n, s));
+        k_round_place<<<grid, 256, 0, s>>>(n, g->rnd, r, fpos, start, g->old_of); note_launch();
+        CUSTEP(cudaGetLastError());
+        CUSTEP(cudaMemsetAsync(hist + r, 0, 4, s));
+    }
     // rows = rounds; sort the members of each round by id (distinct ids)
     STEP(segmented_sort_unique(g->old_of, tmp, start, hist, rdeg, R, n, s));
     k_invert<<<grid, 256, 0, s>>>(n, g->old_of, g->new_of, g->off, rdeg); note_launch();

@@ -185,13 +185,27 @@ struct SortLists {
     uint32_t* count;   // kClasses counters
 };
 
+// One atomic per class and warp (a warp's rows of one class are appended
+// together; order inside a class does not matter).
 __global__ void k_classify(const uint32_t* len, uint32_t rows, SortLists L) {
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < rows;
-         r += gridDim.x * blockDim.x) {
-        uint32_t l = len[r];
-        int c = l <= kSmallMax ? 0 : l <= kWarpMax ? 4 : l <= kMedMax ? 1 : l <= kLargeMax ? 2 : 3;
-        uint32_t at = atomicAdd(&L.count[c], 1u);
-        L.rows[c][at] = r;
+    const unsigned lane = lane_id();
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r0 = blockIdx.x * blockDim.x; r0 < rows; r0 += stride) {
+        const uint32_t r = r0 + threadIdx.x;
+        int c = -1;
+        if (r < rows) {
+            const uint32_t l = len[r];
+            c = l <= kSmallMax ? 0 : l <= kWarpMax ? 4 : l <= kMedMax ? 1 : l <= kLargeMax ? 2 : 3;
+        }
+#pragma unroll
+        for (int q = 0; q < kClasses; q++) {
+            const unsigned b = __ballot_sync(0xffffffffu, c == q);
+            if (!b) continue;
+            uint32_t base = 0;
+            if (lane == (unsigned)(__ffs(b) - 1)) base = atomicAdd(&L.count[q], (uint32_t)__popc(b));
+            base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+            if (c == q) L.rows[q][base + __popc(b & ((1u << lane) - 1u))] = r;
+        }
     }
 }
 
