@@ -108,6 +108,14 @@ dsd_status dsd_set_peel_tail_limit(uint32_t max_alive);
  * 0: the scan alone).  Results do not depend on it.  Process-wide; applies
  * to calls started afterwards.  Never fails. */
 dsd_status dsd_set_peel_app_queue(uint32_t shared_words, uint64_t global_words);
+/* Work items of the peel for h >= 4 (the cliques through one frontier vertex
+ * v whose smallest other member is w): a warp lists those of a candidate set
+ * of at most `warp_max` vertices itself (2..32, default 4); sets of up to 32
+ * go, with their candidates, to groups of 8 warps, at most `mid_max` per
+ * round (default 2^20; 0: none); larger ones, and any beyond mid_max, to a
+ * whole block.  Results do not depend on it.  Process-wide; applies to calls
+ * started afterwards.  DSD_ERR_INVALID for warp_max outside 2..32. */
+dsd_status dsd_set_peel_items(uint32_t warp_max, uint32_t mid_max);
 
 /* Checked mode (off by default; process-wide, for calls started
  * afterwards).  Clique-degrees and mu are exact unsigned 64-bit integers;

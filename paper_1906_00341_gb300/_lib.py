@@ -90,6 +90,7 @@ SIGNATURES = {
     "dsd_set_peel_small_limit": (_int, [_u32]),
     "dsd_set_peel_tail_limit": (_int, [_u32]),
     "dsd_set_peel_app_queue": (_int, [_u32, ctypes.c_uint64]),
+    "dsd_set_peel_items": (_int, [_u32, _u32]),
     "dsd_graph_from_edges": (_int, [_u32, _u64, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_from_csr": (_int, [_u32, _P, _P, _int, _P, ctypes.POINTER(_P)]),
     "dsd_graph_destroy": (None, [_P]),
@@ -229,6 +230,10 @@ def dsd_set_peel_tail_limit(max_alive):
 
 def dsd_set_peel_app_queue(shared_words, global_words):
     _check(load().dsd_set_peel_app_queue(shared_words, global_words))
+
+
+def dsd_set_peel_items(warp_max, mid_max):
+    _check(load().dsd_set_peel_items(warp_max, mid_max))
 
 
 def dsd_graph_from_edges(n, m, src_ptr, dst_ptr, mem, stream_ptr):

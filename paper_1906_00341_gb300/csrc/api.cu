@@ -23,6 +23,11 @@ static std::atomic<unsigned long long> g_app_qglobal{64ull << 20};
 uint32_t peel_app_queue_shared() { return g_app_qshared.load(); }
 uint64_t peel_app_queue_global() { return g_app_qglobal.load(); }
 
+static std::atomic<uint32_t> g_item_warp{4};
+static std::atomic<uint32_t> g_item_mid{1u << 20};
+uint32_t peel_item_warp_limit() { return g_item_warp.load(); }
+uint32_t peel_item_mid_limit() { return g_item_mid.load(); }
+
 static std::atomic<int> g_checked{0};
 bool checked_mode() { return g_checked.load() != 0; }
 
@@ -369,6 +374,16 @@ dsd_status dsd_set_peel_tail_limit(uint32_t max_alive) {
 dsd_status dsd_set_peel_app_queue(uint32_t shared_words, uint64_t global_words) {
     g_app_qshared = shared_words < 12288 ? shared_words : 12288;
     g_app_qglobal = global_words;
+    return DSD_OK;
+}
+
+dsd_status dsd_set_peel_items(uint32_t warp_max, uint32_t mid_max) {
+    if (warp_max < 2 || warp_max > 32) {
+        set_error("dsd_set_peel_items: warp_max must be 2..32 (got %u)", warp_max);
+        return DSD_ERR_INVALID;
+    }
+    g_item_warp = warp_max;
+    g_item_mid = mid_max;
     return DSD_OK;
 }
 

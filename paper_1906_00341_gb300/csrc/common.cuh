@@ -58,6 +58,8 @@ uint32_t peel_small_limit();
 uint32_t peel_tail_limit();
 uint32_t peel_app_queue_shared();   // PeelApp bucket queues: shared-memory words per block
 uint64_t peel_app_queue_global();   // and global-memory words in all
+uint32_t peel_item_warp_limit();    // h >= 4 peel: candidate sets a warp lists itself
+uint32_t peel_item_mid_limit();     // and mid items a round may queue for warp groups
 
 // --------------------------------------------------------- device utils
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -65,11 +65,15 @@ constexpr uint32_t kWarpWords = 3 * kWarpCand;   // a warp's candidates, counter
 constexpr uint32_t kMidWords = 3 + kWarpCand;    // a mid item: v, w, |C|, C
 constexpr int kGroupWarps = 8;                    // warps of a group taking one mid item
 // h >= 4: a warp lists the cliques of a candidate set of at most this many
-// vertices itself; larger sets go to a whole block after the next grid
-// barrier.  Items are the round's critical path when one warp walks the rows
-// of many candidates in turn: on R-MAT scale 21 the peel took 9.4 s (h = 4)
-// and 20.5 s (h = 5) with the limit at 32, 5.2 s and 13.5 s at 4.
-__host__ __device__ inline uint32_t warp_cand_limit(int h) { return h >= 4 ? 4u : kWarpCand; }
+// vertices itself (default 4, dsd_set_peel_items); larger sets go to a warp
+// group or a whole block after the next grid barrier.  Items are the round's
+// critical path when one warp walks the rows of many candidates in turn: on
+// R-MAT scale 21 the peel took 9.4 s (h = 4) and 20.5 s (h = 5) with the limit
+// at 32, 5.2 s and 13.5 s at 4.
+inline uint32_t warp_cand_limit(int h) {
+    uint32_t w = peel_item_warp_limit();
+    return h >= 4 ? (w < kWarpCand ? w : kWarpCand) : kWarpCand;
+}
 constexpr uint32_t kHeavyBit = 4;       // state word: frontier vertex on the heavy list
 constexpr uint32_t kSlotShift = 3;      // state word: 1 + its neighbourhood bitmap slot
 constexpr uint32_t kSlotMask = 0xffu;
@@ -1642,10 +1646,10 @@ __global__ void k_barrier_probe(PeelCtrl* c, uint64_t wait_ns, int absent) {
 
 template <int NT>
 cudaError_t launch_peel(PeelParams& P, int sms, size_t smem, cudaStream_t s, unsigned* grid_out) {
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024)
-        e = cudaFuncSetAttribute(k_peel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+    // opt in for every launch: the 48 KB default bounds static + dynamic
+    // shared memory together, and the attribute persists across calls
+    cudaError_t e = cudaFuncSetAttribute(k_peel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel<NT>, NT, smem);
@@ -1779,8 +1783,9 @@ dsd_status run_peel(dsd_graph* g, int h, uint32_t n, const uint64_t* off, const 
         if ((st = dalloc(&big, P.big_cap, s)) != DSD_OK) goto done;
         // mid items (sets of warp_cand + 1 .. 32 candidates): up to 2^20 per
         // round (144 MB), the rest as big items
-        const uint64_t mc = P.big_cap < (1u << 20) ? P.big_cap : (1u << 20);
-        if (P.warp_cand < kWarpCand) {
+        uint64_t mc = P.big_cap < (1u << 20) ? P.big_cap : (1u << 20);
+        if (mc > peel_item_mid_limit()) mc = peel_item_mid_limit();
+        if (P.warp_cand < kWarpCand && mc > 0) {
             if ((st = dalloc(&mid, (size_t)mc * kMidWords, s)) != DSD_OK) goto done;
             P.mid = mid;
             P.mid_cap = (uint32_t)mc;

@@ -779,9 +779,9 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
         P.err = stepv + n + 1;
         size_t smem = (words + qsh) * 4;
         const void* fn = (const void*)k_peel_app<kAppNT>;
-        if (smem > 48 * 1024)
-            APP_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+        // opt in for every launch: the 48 KB default bounds static + dynamic
+        // shared memory together
+        APP_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per = 0;
         APP_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_peel_app<kAppNT>, kAppNT,
                                                              smem));

@@ -175,3 +175,17 @@ def test_checked_mode_switch_without_gpu(lib):
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
     rc = lib.dsd_batch_run(-1, None, None, None, None, None)
     assert _lib.STATUS[rc] == "DSD_ERR_INVALID"
+
+
+def test_tuning_switches_without_gpu(lib):
+    from paper_1906_00341_gb300 import _lib
+    # the peel's item thresholds: warp_max outside 2..32 is rejected, the
+    # defaults are restored; the PeelApp queue placement never fails
+    for bad in (0, 1, 33):
+        with pytest.raises(_lib.DSDError) as ei:
+            _lib.dsd_set_peel_items(bad, 16)
+        assert ei.value.name == "DSD_ERR_INVALID"
+    _lib.dsd_set_peel_items(2, 0)
+    _lib.dsd_set_peel_items(4, 1 << 20)
+    _lib.dsd_set_peel_app_queue(0, 0)
+    _lib.dsd_set_peel_app_queue(12288, 1 << 26)

@@ -255,3 +255,35 @@ def test_er2000_bruteforce_subsamples(L, orc):
             for h in (2, 3):
                 core, _ = g.core_decompose(h)
                 assert core.astype(np.int64).tolist() == bf.core_numbers(A, h).tolist()
+
+
+_ITEM_CASES = {}
+
+
+def _item_cases(orc):
+    """Graphs for the item-path test and the oracle's core numbers (computed once)."""
+    if not _ITEM_CASES:
+        graphs = [gg.workload("rmat14")[:3]] + [gg.random_small(300, 0.12, seed=970 + i)
+                                                 for i in range(3)]
+        for gi, (n, s, d) in enumerate(graphs):
+            og = orc.csr(n, s, d)
+            for h in (4, 5):
+                _ITEM_CASES[(gi, h)] = ((n, s, d), orc.core_decompose(og, h))
+    return _ITEM_CASES
+
+
+@pytest.mark.parametrize("warp_max,mid_max", [(32, 0), (4, 0), (4, 1), (2, 1 << 20), (8, 16)])
+def test_peel_item_paths(L, orc, warp_max, mid_max):
+    """h >= 4: the work items of the peel listed by a warp, by a group of
+    warps (mid items, with the list overflowing at mid_max) or by a block
+    give the oracle's core numbers whatever the thresholds."""
+    cases = _item_cases(orc)
+    L.dsd_set_peel_items(warp_max, mid_max)
+    try:
+        for (gi, h), ((n, s, d), (wcore, wk)) in cases.items():
+            with L.Graph.from_edges(n, s, d) as g:
+                core, kmax = g.core_decompose(h)
+            assert kmax == wk, (gi, h)
+            assert np.array_equal(core, wcore), (gi, h)
+    finally:
+        L.dsd_set_peel_items(4, 1 << 20)
