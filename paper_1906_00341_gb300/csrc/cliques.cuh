@@ -285,8 +285,11 @@ __device__ __forceinline__ void block_build_rows(const uint32_t* C, uint32_t nc,
 // Warps take first members i from the shared counter *next_i (zero on
 // entry; the early candidates, with the largest searches below them, go
 // first); lane l holds word l of the current sets (and the bit-sliced
-// counters of candidates 32 l .. 32 l + 31).  Returns this thread's share of
-// the total (sum over the block = total).
+// counters of candidates 32 l .. 32 l + 31).  Rows of at most 16 words leave
+// lanes idle in the leaf loop, so there the warp takes G = 32 / W2 leaves at
+// a time (W2 = W rounded up to a power of two): lane l works on word l % W2
+// of leaf l / W2 and keeps the bit-sliced counters of that word.  Returns
+// this thread's share of the total (sum over the block = total).
 __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, uint32_t nc,
                                                        uint32_t W, int r,
                                                        unsigned long long* cnt,
@@ -294,6 +297,12 @@ __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, ui
     const unsigned full = 0xffffffffu;
     unsigned lane = lane_id();
     unsigned long long total = 0;
+    // leaf packing: W2 lanes per leaf, G leaves per step
+    uint32_t W2 = 1;
+    while (W2 < W) W2 <<= 1;
+    const uint32_t G = W2 <= 16 ? 32 / W2 : 1;
+    const uint32_t lw = G > 1 ? lane % W2 : lane;   // the word this lane works on
+    const uint32_t slot = G > 1 ? lane / W2 : 0;
     BitSliced bs;
     bs.clear();
     for (;;) {
@@ -312,8 +321,8 @@ __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, ui
         unsigned pc = __reduce_add_sync(full, (unsigned)__popc(P[1]));
         if ((int)pc < r - 1) continue;
         if (r == 2) {
-            bs.add(P[1]);
-            if (bs.adds == kSliceAdds) bs.flush(cnt + lane * 32);
+            bs.add(G > 1 ? __shfl_sync(full, P[1], lw) * (slot == 0) : P[1]);
+            if (bs.adds == kSliceAdds) bs.flush(cnt + lw * 32);
             if (lane == 0) {
                 atomicAdd(&cnt[i], (unsigned long long)pc);
                 total += pc;
@@ -321,7 +330,37 @@ __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, ui
             continue;
         }
         while (depth >= 1) {
-            if (depth == r - 2) {
+            if (depth == r - 2 && G > 1) {
+                // packed leaves: slot q of each step takes the q-th next j
+                const uint32_t Pw = __shfl_sync(full, P[depth], lw);
+                uint32_t rm = rem[depth];
+                unsigned long long sub = 0;
+                for (;;) {
+                    uint32_t myj = 0xffffffffu;
+                    uint32_t got = 0;
+                    for (uint32_t q = 0; q < G; q++) {
+                        const unsigned have = __ballot_sync(full, rm != 0);
+                        if (!have) break;
+                        const int fl = __ffs(have) - 1;
+                        const uint32_t word = __shfl_sync(full, rm, fl);
+                        const uint32_t j = (uint32_t)fl * 32 + (__ffs(word) - 1);
+                        if ((int)lane == fl) rm &= rm - 1;
+                        if (slot == q) myj = j;
+                        got++;
+                    }
+                    if (!got) break;
+                    const uint32_t last =
+                        (myj != 0xffffffffu && lw < W) ? Pw & rows[myj * W + lw] : 0u;
+                    unsigned c = __popc(last);
+                    for (uint32_t o = W2 >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(full, c, o);
+                    bs.add(last);
+                    if (bs.adds == kSliceAdds) bs.flush(cnt + lw * 32);
+                    const unsigned lead_c = lw == 0 ? c : 0u;
+                    if (lead_c) atomicAdd(&cnt[myj], (unsigned long long)lead_c);
+                    sub += __reduce_add_sync(full, lead_c);
+                }
+                acc[depth] += sub;
+            } else if (depth == r - 2) {
                 // every j left in rem is member r-1, its leaf mask the last members
                 const uint32_t Pd = P[depth];
                 uint32_t rm = rem[depth];
@@ -337,7 +376,7 @@ __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, ui
                     unsigned c = __reduce_add_sync(full, (unsigned)__popc(last));
                     if (c) {
                         bs.add(last);
-                        if (bs.adds == kSliceAdds) bs.flush(cnt + lane * 32);
+                        if (bs.adds == kSliceAdds) bs.flush(cnt + lw * 32);
                         if (lane == 0) atomicAdd(&cnt[j], (unsigned long long)c);
                         sub += c;
                     }
@@ -372,7 +411,7 @@ __device__ __forceinline__ unsigned long long block_dfs(const uint32_t* rows, ui
             depth--;
         }
     }
-    bs.flush(cnt + lane * 32);
+    bs.flush(cnt + lw * 32);
     return lane == 0 ? total : 0ull;
 }
 
