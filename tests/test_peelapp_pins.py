@@ -97,3 +97,19 @@ def test_peelapp_closed_forms(orc):
     # no triangle: the whole graph, density 0
     r = orc.peel_app(orc.csr(4, np.array([0, 1, 2], np.uint32), np.array([1, 2, 3], np.uint32)), 3)
     assert r["mu"] == 0 and r["size"] == 4
+
+
+@pytest.mark.parametrize("h", [2, 3, 4])
+def test_peelapp_removes_the_levels_in_order(orc, h):
+    """The fact the GPU's per-level PeelApp rests on: the one-at-a-time peel
+    removes every vertex of core number k before any of core number k + 1
+    (the minimum is always taken outside R_{k+1}), so its removal order is
+    sorted by the (k,Psi)-core numbers of Algorithm 3."""
+    for seed in range(4):
+        n, s, d = gg.er(150, 0.06 + 0.02 * seed, 9950 + seed)
+        n, s, d, _ = gg.plant(n, s, d, 14, 0.8, 9960 + seed)
+        g = orc.csr(n, s, d)
+        order = np.asarray(orc.peel_app(g, h)["order"], np.int64)
+        core, _ = orc.core_decompose(g, h)
+        assert sorted(order.tolist()) == list(range(n))
+        assert np.all(np.diff(np.asarray(core, np.int64)[order]) >= 0), (h, seed)
