@@ -39,14 +39,16 @@ def _simulate(A, h):
                    if all(A[v, x] for x in c) and all(A[a, b] for a, b in itertools.combinations(c, 2)))
 
     best_set, best = set(alive), Fraction(count_in(alive), n) if n else Fraction(0)
+    order = []
     while alive:
         v = min(alive, key=lambda x: (deg_in(alive, x), x))
+        order.append(v)
         alive.remove(v)
         if alive:
             d = Fraction(count_in(alive), len(alive))
             if d > best:
                 best, best_set = d, set(alive)
-    return best_set, best
+    return best_set, best, order
 
 
 @pytest.mark.parametrize("h", [2, 3, 4])
@@ -58,9 +60,11 @@ def test_peelapp_simulation(orc, h):
         g = orc.csr(n, s, d)
         A = bf.adjacency(n, g.off, g.adj)
         r = orc.peel_app(g, h)
-        want_set, want = _simulate(A, h)
+        want_set, want, want_order = _simulate(A, h)
         assert r["set"].tolist() == sorted(want_set), (h, i)
         assert Fraction(r["mu"], r["size"]) == want
+        # the whole removal order, ties to the smaller id
+        assert np.asarray(r["order"]).tolist() == want_order, (h, i)
         # Lemma 2 against brute force
         rho_opt = bf.rho_opt(A, h)
         assert Fraction(r["mu"], r["size"]) >= rho_opt / h
