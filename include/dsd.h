@@ -322,10 +322,10 @@ typedef struct {
  *   order (capacity n, may be NULL): the removal order, order[i] = the
  *       vertex removed at step i;
  *   both host or device memory per mem; res must not be NULL.
- * With n = 0 all fields are 0.  Errors: DSD_ERR_INVALID; DSD_ERR_UNSUPPORTED
- * (h >= 4 with more than 1024 higher-ranked neighbours at a vertex);
- * DSD_ERR_NOMEM; DSD_ERR_TIMEOUT (the decomposition's wait limit);
- * DSD_ERR_CUDA. */
+ * Candidate sets of more than 1024 vertices (degeneracy above 1024, h >= 4)
+ * are split by their next member, as in the decomposition.
+ * With n = 0 all fields are 0.  Errors: DSD_ERR_INVALID; DSD_ERR_NOMEM;
+ * DSD_ERR_TIMEOUT (the decomposition's wait limit); DSD_ERR_CUDA. */
 dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint32_t* order, int mem,
                         dsd_peel_app_result* res);
 

@@ -42,8 +42,8 @@
 // cleared lazily by the search.  Members of count 0 lie in no h-clique of
 // the current set, so their removal changes no count: they leave one after
 // another in position order without the clique listing.
-#include "cliques.cuh"
 #include "graph.cuh"
+#include "xl.cuh"
 
 #include <algorithm>
 #include <string.h>
@@ -78,6 +78,8 @@ struct AppParams {
     uint32_t* bigw;           // per block: bigcap entries
     uint32_t bigcap;
     uint32_t cap;             // big candidate sets: >= max |N+|, >= 32
+    uint32_t bcap;            // shared-memory candidate sets: min(cap, kBitmapMax)
+    uint32_t* xl;             // per block (kMaxDepth + 1) * cap entries when cap > kBitmapMax
     uint32_t qwords;          // shared words of the bucket queue (after the scratch)
     uint32_t scratch_words;   // shared words of the warp and big-set scratch
     const uint32_t* qB;       // per level: buckets B (0 = no queue: the scan)
@@ -227,23 +229,60 @@ __device__ bool app_item(const AppParams& P, const AppQ& Q, uint32_t v, uint32_t
 }
 
 // A candidate set above kAppWarpCand vertices (h >= 4): the whole block,
-// bitmap rows of G[C] and the block DFS.
+// bitmap rows of G[C] and the block DFS.  When N+(w) holds more than
+// kBitmapMax entries (degeneracy above 1024) the candidates are gathered in
+// order into the block's global scratch, and a set that still exceeds
+// kBitmapMax is split by its next member (xl.cuh), as in the peel.
 __device__ void app_big(const AppParams& P, const AppQ& Q, uint32_t v, uint32_t w,
                         unsigned long long k, uint32_t* smem) {
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);   // cap
-    uint32_t* C = smem + 2 * P.cap;                                            // cap
-    uint32_t* rows = C + P.cap;                                                // cap * W
-    __shared__ uint32_t s_nc, s_next;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem);   // bcap
+    uint32_t* C = smem + 2 * P.bcap;                                           // bcap
+    uint32_t* rows = C + P.bcap;                                               // bcap * W
+    __shared__ uint32_t s_nc, s_next, s_w[32], s_t2;
     __shared__ unsigned long long s_tot;
-    if (warp_id() == 0) {
-        uint32_t nc = app_gather<false>(P, Q, v, w, k, C, P.cap);
-        if (lane_id() == 0) {
+    const uint64_t wb = P.split[w], we = P.off[w + 1];
+    if (we - wb > kBitmapMax) {
+        uint32_t* G0 = P.xl + (size_t)blockIdx.x * (kMaxDepth + 1) * P.cap;
+        const uint32_t* Nv = P.adj + P.off[v];
+        const uint64_t dv = P.off[v + 1] - P.off[v];
+        const uint32_t nc = block_filter(
+            P.adj + wb, we - wb, G0,
+            [&](uint32_t x) {
+                if (!in_set(P, x, k)) return false;
+                uint64_t pos = lower_bound_u32(Nv, dv, x);
+                return pos < dv && Nv[pos] == x;
+            },
+            s_w, &s_t2);
+        if (threadIdx.x == 0) s_tot = 0;
+        __syncthreads();
+        if (nc < (uint32_t)(P.h - 2)) return;
+        if (nc > kBitmapMax) {
+            xl_cliques(
+                G0, nc, P.h - 2, P.split, P.off + 1, P.adj, G0 + P.cap, P.cap, smem,
+                [&](uint32_t x, unsigned long long c) { lower(P, Q, x, k, c); },
+                [&](unsigned long long c) { s_tot += c; });
+            __syncthreads();
+            if (threadIdx.x == 0) lower(P, Q, w, k, s_tot);
+            __syncthreads();
+            return;
+        }
+        for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) C[i] = G0[i];
+        if (threadIdx.x == 0) {
             s_nc = nc;
             s_next = 0;
-            s_tot = 0;
         }
+        __syncthreads();
+    } else {
+        if (warp_id() == 0) {
+            uint32_t nc = app_gather<false>(P, Q, v, w, k, C, P.bcap);
+            if (lane_id() == 0) {
+                s_nc = nc;
+                s_next = 0;
+                s_tot = 0;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const uint32_t nc = s_nc, W = (nc + 31) >> 5;
     for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) cnt[i] = 0;
     for (uint32_t i = threadIdx.x; i < nc * W; i += blockDim.x) rows[i] = 0;
@@ -613,11 +652,6 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
     DSD_TRY(ensure_order(g));
     const uint32_t n = g->n;
     if (n == 0) return DSD_OK;
-    if (h >= 4 && g->maxdplus > kBitmapMax) {
-        set_error("h=%d PeelApp needs at most %u higher-ranked neighbours per vertex (max %u)", h,
-                  kBitmapMax, g->maxdplus);
-        return DSD_ERR_UNSUPPORTED;
-    }
     cudaStream_t s = g->stream;
     int sms = 152;
     DSD_TRY(num_sms(&sms));
@@ -638,7 +672,7 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
     uint32_t nl = 0;
     std::vector<uint32_t> hls, hqB;
     std::vector<uint64_t> hk, hqoff;
-    uint32_t *qBv = nullptr, *qg = nullptr;
+    uint32_t *qBv = nullptr, *qg = nullptr, *xl = nullptr;
     uint64_t* qoffv = nullptr;
     uint32_t herr = 0;
 #define APP_TRY(x)                                \
@@ -724,6 +758,7 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
         P.lm = lm;
         P.nl = nl;
         P.cap = g->maxdplus < 32 ? 32 : g->maxdplus;
+        P.bcap = P.cap < kBitmapMax ? P.cap : kBitmapMax;
         // the counts, steps and queue reuse buffers of the decomposition
         APP_TRY(dalloc(&pdeg, (size_t)n + 1, s));
         APP_TRY(dalloc(&stepv, (size_t)n + 2, s));
@@ -736,8 +771,10 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
         P.best = best;
         size_t words = (size_t)(kAppNT / 32) * 3 * kAppWarpCand;
         if (h >= 4) {
-            size_t W = (P.cap + 31) / 32;
-            size_t big = (size_t)3 * P.cap + (size_t)P.cap * W;
+            size_t W = (P.bcap + 31) / 32;
+            size_t big = (size_t)3 * P.bcap + (size_t)P.bcap * W;
+            // the split search of oversized sets uses the full bitmap tier layout
+            if (P.cap > kBitmapMax) big = (size_t)3 * kBitmapMax + (size_t)kBitmapMax * 32;
             if (big > words) words = big;
         }
         // bucket queues: in shared memory after the scratch where they fit
@@ -791,6 +828,10 @@ extern "C" dsd_status dsd_peel_app(dsd_graph* g, int h, uint32_t* densest, uint3
             goto done;
         }
         unsigned grid = (unsigned)(sms * per);
+        if (h >= 4 && P.cap > kBitmapMax) {
+            APP_TRY(dalloc(&xl, (size_t)grid * (kMaxDepth + 1) * P.cap, s));
+            P.xl = xl;
+        }
         // a removal lists at most deg(v) big candidate sets: the per-block
         // list holds the largest row
         unsigned long long maxrow = 0;
@@ -867,7 +908,7 @@ done:
                     (void*)lev, (void*)cur, (void*)ids, (void*)tmp, (void*)lenv, (void*)newlen,
                     (void*)lpos, (void*)rank_at, (void*)posof, (void*)pdeg, (void*)stepv,
                     (void*)best, (void*)pick, (void*)lorder, (void*)bigw, (void*)flag,
-                    (void*)pos, (void*)obuf, (void*)qBv, (void*)qoffv, (void*)qg})
+                    (void*)pos, (void*)obuf, (void*)qBv, (void*)qoffv, (void*)qg, (void*)xl})
         dev_free(p, s);
     return st;
 }

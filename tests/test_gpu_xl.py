@@ -71,3 +71,18 @@ def test_bipartite_plus_against_oracle(L, orc, h):
     assert np.array_equal(r["kmax_core"], w["kmax_core"])
     assert np.array_equal(r["densest"], w["densest"])
     assert (r["densest_mu"], r["densest_size"]) == (w["densest_mu"], w["densest_size"])
+
+
+def test_peelapp_bipartite_plus_against_oracle(L, orc):
+    """PeelApp (Algorithm 2) at h = 4 on a graph of degeneracy above 1024:
+    its big candidate sets take the split tier; the set, its density and the
+    whole removal order equal the oracle's one-at-a-time peel."""
+    n, s, d = bipartite_plus(1100, 3000, seed=45)
+    og = orc.csr(n, s, d)
+    w = orc.peel_app(og, 4)
+    with L.Graph.from_edges(n, s, d) as g:
+        assert g.degeneracy_order()[2] > 1024
+        r = g.peel_app(4)
+    assert (r["mu"], r["size"]) == (w["mu"], w["size"])
+    assert np.array_equal(np.asarray(r["order"]).astype(np.uint32), w["order"])
+    assert np.array_equal(np.asarray(r["set"]).astype(np.uint32), w["set"])
